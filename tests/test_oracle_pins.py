@@ -1,0 +1,454 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types the oracle's formulas: each checks a closed form, an
+invariant, a constructed ground truth, a hand-derived fixture
+(tests/golden/) or brute force on tiny inputs, chosen so that a dropped term,
+a wrong sign or index, or a transposed operand in the oracle fails one of
+them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import cloth_scenes as cs
+from helpers import (GOLDEN, floor_mesh, make_scene, pair_type, ray_parity_inside, spring_energy,
+                     stencil_pairs)
+
+
+# ------------------------------------------------------------ spring layout
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 2), (2, 1), (3, 3), (4, 7), (6, 5)])
+def test_spring_enumeration_matches_brute_force_pairs(oracle_lib, nx, ny):
+    a, b, t = oracle_lib.springs(nx, ny)
+    got = {(min(i, j), max(i, j)) for i, j in zip(a.tolist(), b.tolist())}
+    assert len(got) == len(a), "duplicate spring"
+    assert got == stencil_pairs(nx, ny)
+    assert len(a) == cs.spring_count(nx, ny)
+    for i, j, ty in zip(a.tolist(), b.tolist(), t.tolist()):
+        assert ty == pair_type(nx, i, j)
+    # canonical order: node1 row-major ascending
+    assert np.all(np.diff(a) >= 0)
+
+
+def test_spring_counts_of_the_workloads():
+    # structural 2n(n-1), shear 2(n-1)^2, bend 2n(n-2)
+    for n, S in [(32, 5826), (128, 97026), (256, 390658), (800, 3832002)]:
+        assert cs.spring_count(n, n) == S == 2 * n * (n - 1) + 2 * (n - 1) ** 2 + 2 * n * (n - 2)
+
+
+# ------------------------------------------------------------ force law (Alg. 1)
+
+def test_zero_force_at_rest_length(oracle_lib):
+    # dyadic spacing: every rest length and current length is computed from
+    # identical exact differences, so Hooke's term is exactly zero; a uniform
+    # velocity makes every damping term exactly zero too.
+    sc = make_scene(9, 7, du=(0.125, 0.0, 0.0), dv=(0.0, 0.0, 0.125), ks=(500, 250, 100), kd=(0.5, 0.3, 0.2))
+    cl = oracle_lib.Cloth(sc)
+    x = sc.init_pos.astype(np.float64)
+    v = np.tile([0.5, -1.25, 2.0], (sc.n, 1))
+    F = oracle_lib.spring_forces(cl, x, v)
+    assert np.all(F == 0.0)
+
+
+def test_momentum_internal_forces_sum_to_zero(oracle_lib):
+    rng = np.random.default_rng(11)
+    sc = make_scene(12, 9, ks=(500, 250, 100), kd=(0.5, 0.3, 0.2))
+    cl = oracle_lib.Cloth(sc)
+    x = sc.init_pos + rng.normal(0, 0.02, (sc.n, 3))
+    v = rng.normal(0, 1.0, (sc.n, 3))
+    F = oracle_lib.spring_forces(cl, x, v)
+    tot = np.abs(F).sum()
+    assert tot > 1.0
+    assert np.all(np.abs(F.sum(axis=0)) <= 1e-12 * tot)
+    # angular momentum: central forces exert no net torque
+    tau = np.cross(x, F).sum(axis=0)
+    assert np.all(np.abs(tau) <= 1e-12 * (np.abs(np.cross(x, F)).sum()))
+
+
+def test_spring_force_is_minus_energy_gradient(oracle_lib):
+    # kd = 0: F_i = -dE/dx_i for E = sum 1/2 k (l - L0)^2 over the brute-force
+    # pair list (central finite differences).
+    rng = np.random.default_rng(3)
+    nx, ny = 5, 4
+    ks = (500.0, 250.0, 100.0)
+    sc = make_scene(nx, ny, ks=ks)
+    X0 = cs.flat_grid(nx, ny, sc.origin, sc.du, sc.dv)
+    x = X0 + rng.normal(0, 0.01, X0.shape)
+    cl = oracle_lib.Cloth(sc)
+    F = oracle_lib.spring_forces(cl, x, np.zeros_like(x))
+    kof = lambda i, j: ks[pair_type(nx, i, j)]
+    h = 1e-6
+    for i in range(sc.n):
+        for k in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, k] += h
+            xm[i, k] -= h
+            g = (spring_energy(nx, ny, X0, xp, kof) - spring_energy(nx, ny, X0, xm, kof)) / (2 * h)
+            assert abs(F[i, k] + g) <= 1e-6 * max(1.0, abs(g)), (i, k, F[i, k], -g)
+
+
+def test_damping_is_dissipative(oracle_lib):
+    # ks = 0: the power of the damping forces, sum F_i . v_i, is never positive
+    rng = np.random.default_rng(5)
+    sc = make_scene(7, 6, kd=(0.5, 0.3, 0.2))
+    cl = oracle_lib.Cloth(sc)
+    for _ in range(5):
+        x = sc.init_pos + rng.normal(0, 0.02, (sc.n, 3))
+        v = rng.normal(0, 1.0, (sc.n, 3))
+        F = oracle_lib.spring_forces(cl, x, v)
+        assert np.sum(F * v) < 0.0
+
+
+def test_two_node_damping_closed_form(oracle_lib):
+    # Two nodes on one structural spring, ks = 0, velocities along the spring:
+    # symplectic Euler gives dv_n = (1 - 2 kd dt / m)^n dv_0 exactly.
+    kd, m, dt, u = 0.3, 0.05, 1e-3, 0.75  # u exact in float32
+    sc = make_scene(2, 1, du=(0.1, 0.0, 0.0), total_mass=2 * m, kd=(kd, 0, 0), dt=dt,
+                    vel=[[-u, 0, 0], [u, 0, 0]])
+    cl = oracle_lib.Cloth(sc)
+    n = 37
+    x, v = oracle_lib.step(cl, sc.init_pos, sc.init_vel, 0, n)
+    dv = v[1, 0] - v[0, 0]
+    assert dv == pytest.approx(2 * u * (1 - 2 * kd * dt / m) ** n, rel=1e-12)
+    assert np.all(v[:, 1:] == 0)
+    # momentum conserved
+    assert abs(v[0, 0] + v[1, 0]) < 1e-15
+
+
+# ------------------------------------------------------------ integrator
+
+def test_free_fall_discrete_closed_form(oracle_lib):
+    # No springs: symplectic Euler gives v_n = v0 + n dt g and
+    # x_n = x0 + n dt v0 + dt^2 g n(n+1)/2 (explicit Euler would give n(n-1)/2).
+    g = np.array([0.3, -9.81, 0.2])
+    v0 = np.array([1.0, 2.0, -0.5])
+    x0 = np.array([0.1, 0.2, 0.3])
+    dt = 1.0 / 4800
+    sc = make_scene(1, 1, origin=x0, gravity=g, dt=dt, vel=[v0])
+    cl = oracle_lib.Cloth(sc)
+    n = 250
+    x, v = oracle_lib.step(cl, sc.init_pos, sc.init_vel, 0, n)
+    x0f = sc.init_pos[0].astype(np.float64)
+    v0f = sc.init_vel[0].astype(np.float64)
+    np.testing.assert_allclose(v[0], v0f + n * dt * g, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(x[0], x0f + n * dt * v0f + dt * dt * g * n * (n + 1) / 2, rtol=0, atol=1e-12)
+
+
+def test_hanging_spring_static_extension(oracle_lib):
+    # One pinned node, one free node of mass m below it on a damped spring:
+    # converges to l = L0 + m g / k.
+    m, k, kd, L0 = 0.05, 50.0, 1.0, 0.1
+    sc = make_scene(1, 2, dv=(0.0, -L0, 0.0), total_mass=2 * m, ks=(k, 0, 0), kd=(kd, 0, 0),
+                    gravity=(0, -9.81, 0), dt=1e-3, pinned=[1, 0])
+    cl = oracle_lib.Cloth(sc)
+    x, v = oracle_lib.step(cl, sc.init_pos, sc.init_vel, 0, 6000)
+    ell = np.linalg.norm(x[1] - x[0])
+    assert ell == pytest.approx(L0 + m * 9.81 / k, rel=1e-9)
+    assert np.all(x[0] == sc.init_pos[0].astype(np.float64))
+
+
+def _energy(oracle_lib, sc, x, v):
+    m = sc.total_mass / sc.n
+    X0 = cs.flat_grid(sc.nx, sc.ny, sc.origin, sc.du, sc.dv)
+    kof = lambda i, j: sc.ks[pair_type(sc.nx, i, j)]
+    return 0.5 * m * np.sum(v * v) + spring_energy(sc.nx, sc.ny, X0, x, kof)
+
+
+def test_energy_drift_first_order(oracle_lib):
+    # kd = 0, no gravity or pins, jittered start: symplectic Euler keeps the
+    # energy error bounded and first order in dt (halves when dt halves).
+    nx = ny = 6
+    base = make_scene(nx, ny, du=(0.1, 0, 0), dv=(0, 0, 0.1), total_mass=0.36, ks=(40.0, 20.0, 8.0))
+    rng = np.random.default_rng(9)
+    x0 = base.init_pos + rng.uniform(-0.01, 0.01, base.init_pos.shape).astype(np.float32)
+    drifts = []
+    T = 0.1
+    for dt in (2e-4, 1e-4, 5e-5):
+        sc = make_scene(nx, ny, du=(0.1, 0, 0), dv=(0, 0, 0.1), total_mass=0.36, ks=(40.0, 20.0, 8.0),
+                        dt=dt, pos=x0)
+        cl = oracle_lib.Cloth(sc)
+        x, v = x0.astype(np.float64), np.zeros_like(x0, dtype=np.float64)
+        E0 = _energy(oracle_lib, sc, x, v)
+        n = int(round(T / dt))
+        chunk = n // 20
+        worst = 0.0
+        for s in range(20):
+            x, v = oracle_lib.step(cl, x, v, s * chunk, chunk)
+            worst = max(worst, abs(_energy(oracle_lib, sc, x, v) - E0) / E0)
+        drifts.append(worst)
+    assert drifts[0] < 0.2
+    r1, r2 = drifts[0] / drifts[1], drifts[1] / drifts[2]
+    assert 1.6 < r1 < 2.5 and 1.6 < r2 < 2.5, drifts
+
+
+def test_pinned_nodes_hold_position_and_zero_velocity(oracle_lib):
+    sc = cs.config1()
+    cl = oracle_lib.Cloth(sc)
+    x, v = oracle_lib.step(cl, sc.init_pos, sc.init_vel + 0.1, 0, 40)
+    pin = sc.pinned.astype(bool)
+    assert np.all(x[pin] == sc.init_pos[pin].astype(np.float64))
+    assert np.all(v[pin] == 0.0)
+    assert np.all(x[~pin] != sc.init_pos[~pin].astype(np.float64))
+
+
+def test_wind_matches_integrated_sinusoid(oracle_lib):
+    # One free node under wind only: the discrete velocity is a left Riemann
+    # sum of w(t), within T*max|w'|*dt/2 of the exact integral
+    # -A/(2 pi f) [cos(2 pi f T + c) - cos(c)], c = kappa (udir . X0) + phase.
+    w = cs.wind_config3()
+    X0 = np.array([0.3, -0.7, 0.1])
+    dt = 1.0 / 4800
+    n = 2400
+    sc = make_scene(1, 1, origin=X0, dt=dt, wind=w)
+    cl = oracle_lib.Cloth(sc)
+    x, v = oracle_lib.step(cl, sc.init_pos, sc.init_vel, 0, n)
+    c = w.kappa * float(np.dot(w.udir, X0)) + w.phase
+    T = n * dt
+    om = 2 * math.pi * w.freq
+    exact = -w.amp / om * (math.cos(om * T + c) - math.cos(c))
+    bound = T * w.amp * om * dt / 2
+    assert abs(v[0, 2] - exact) <= bound
+    assert abs(exact) > 50 * bound
+    assert v[0, 0] == 0.0 and v[0, 1] == 0.0
+    # the node at a different rest position sees a different phase
+    sc2 = make_scene(1, 1, origin=X0 + np.array([0.125, 0.0, 0.0]), dt=dt, wind=w)
+    x2, v2 = oracle_lib.step(oracle_lib.Cloth(sc2), sc2.init_pos, sc2.init_vel, 0, n)
+    c2 = c + w.kappa * w.udir[0] * 0.125
+    exact2 = -w.amp / om * (math.cos(om * T + c2) - math.cos(c2))
+    assert abs(v2[0, 2] - exact2) <= bound
+
+
+# ------------------------------------------------------------ MT test
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                p = line.split()
+                rows.append((p[0], [float(z) for z in p[1:]]))
+    return rows
+
+
+@pytest.mark.parametrize("name,vals", _golden("mt_cases.txt"))
+def test_mt_golden_cases(oracle_lib, name, vals):
+    S, E = vals[0:3], vals[3:6]
+    hit, t = int(vals[6]), vals[7]
+    V0, V1, V2 = [0, 0, 0], [1, 0, 0], [0, 1, 0]
+    got = oracle_lib.mt(S, E, V0, V1, V2, 1e-7)
+    if hit:
+        assert got is not None and got == pytest.approx(t, rel=1e-15, abs=1e-15)
+    else:
+        assert got is None
+
+
+def test_mt_constructed_hits_and_misses(oracle_lib):
+    # Ground truth by construction: P = V0 + u e1 + v e2 inside the triangle,
+    # S = P - t0 r; the segment S -> S + L r hits at t0 iff L > t0.
+    rng = np.random.default_rng(21)
+    nhit = nmiss = 0
+    for _ in range(3000):
+        V = rng.normal(0, 1, (3, 3))
+        e1, e2 = V[1] - V[0], V[2] - V[0]
+        n = np.cross(e1, e2)
+        if np.linalg.norm(n) < 0.1:
+            continue
+        r = rng.normal(0, 1, 3)
+        r /= np.linalg.norm(r)
+        if abs(np.dot(r, n)) / np.linalg.norm(n) < 0.2:
+            continue
+        u, v = rng.uniform(0, 1, 2)
+        t0 = rng.uniform(0.01, 1.0)
+        inside = rng.uniform() < 0.5
+        if inside:
+            if u + v > 1:
+                u, v = 1 - u, 1 - v
+            u, v = 0.02 + 0.96 * u, 0.02 + 0.96 * v
+            if u + v > 0.98:
+                continue
+        else:
+            # clearly outside: one barycentric coordinate negative or sum > 1
+            choice = rng.integers(3)
+            if choice == 0:
+                u = -0.05 - u
+            elif choice == 1:
+                v = -0.05 - v
+            else:
+                u, v = u + 0.6, v + 0.6
+        P = V[0] + u * e1 + v * e2
+        S = P - t0 * r
+        long_ = rng.uniform() < 0.5
+        L = t0 * (1.05 + rng.uniform()) if long_ else t0 * rng.uniform(0.1, 0.95)
+        E = S + L * r
+        got = oracle_lib.mt(S, E, V[0], V[1], V[2], 1e-7)
+        if inside and long_:
+            assert got is not None and got == pytest.approx(t0, rel=1e-9, abs=1e-12)
+            nhit += 1
+        else:
+            assert got is None
+            nmiss += 1
+    assert nhit > 300 and nmiss > 1000
+
+
+# ------------------------------------------------------------ response (Alg. 2)
+
+@pytest.mark.parametrize("name,vals", _golden("response_cases.txt"))
+def test_response_golden_cases(oracle_lib, name, vals):
+    S, V, K = vals[0:3], vals[3:6], int(vals[6])
+    X, W = vals[7:10], vals[10:13]
+    sc = make_scene(1, 1, origin=S, dt=2.0 ** -10, vel=[V], mesh=floor_mesh(), delta=1e-4)
+    cl = oracle_lib.Cloth(sc)
+    grid = oracle_lib.Grid(*floor_mesh())
+    for brute in (False, True):
+        x, v, hits = oracle_lib.step(cl, sc.init_pos, sc.init_vel, 0, 1, grid, brute=brute, want_hits=True)
+        assert hits[0] == K
+        np.testing.assert_allclose(x[0], X, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(v[0], W, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("y0", [0.05, 0.0507])
+def test_falling_node_lands_on_plane_closed_form(oracle_lib, y0):
+    # Gravity only, node released at height y0 above the floor: free fall in
+    # closed form until the substep whose segment crosses y = 0, where the
+    # node stops delta before the crossing (or stays put when it started
+    # closer than delta) and its velocity flips by -0.5.
+    g, dt, delta = -9.81, 1.0 / 4800, 1e-4
+    sc = make_scene(1, 1, origin=(0.3, y0, 0.6), gravity=(0, g, 0), dt=dt, mesh=floor_mesh(), delta=delta)
+    cl = oracle_lib.Cloth(sc)
+    grid = oracle_lib.Grid(*floor_mesh())
+    y0f = float(sc.init_pos[0, 1])
+    ypos = lambda n: y0f + dt * dt * g * n * (n + 1) / 2
+    n_hit = next(n for n in range(1, 100000) if ypos(n) < 0)
+    x, v = oracle_lib.step(cl, sc.init_pos, sc.init_vel, 0, n_hit - 1, grid)
+    assert x[0, 1] == pytest.approx(ypos(n_hit - 1), abs=1e-12)
+    x, v, hits = oracle_lib.step(cl, x, v, n_hit - 1, 1, grid, want_hits=True)
+    assert hits[0] == 1
+    assert x[0, 1] == pytest.approx(min(ypos(n_hit - 1), delta), abs=1e-12)
+    assert v[0, 1] == pytest.approx(-0.5 * dt * g * n_hit, rel=1e-12)
+    assert x[0, 0] == float(sc.init_pos[0, 0]) and x[0, 2] == float(sc.init_pos[0, 2])
+
+
+# ------------------------------------------------------------ broad phase
+
+def _tiny_meshes():
+    yield cs.sphere_mesh(0, 0.3)
+    yield cs.sphere_mesh(1, 0.25, (0.1, -0.05, 0.02))
+    yield cs.sphere_mesh(2, 0.3, (0.0, -0.5, 0.0), 0.05, 4)
+    yield floor_mesh()
+
+
+@pytest.mark.parametrize("mi", range(4))
+def test_grid_lists_exactly_the_overlapped_cells(oracle_lib, mi):
+    verts, tris = list(_tiny_meshes())[mi]
+    g = oracle_lib.Grid(verts, tris)
+    p = g.params
+    h, o, dims = float(p["h"]), np.array(p["origin"], np.float64), p["dims"]
+    cs_, ids = g.cell_start(), g.tri_ids()
+    assert cs_[0] == 0 and cs_[-1] == len(ids) and np.all(np.diff(cs_) >= 0)
+    lists = [ids[cs_[c]:cs_[c + 1]] for c in range(len(cs_) - 1)]
+    for L in lists:
+        assert np.all(np.diff(L) > 0), "ascending, unique"
+    # no spurious entries: each listed triangle's AABB touches the cell box
+    V = verts.astype(np.float64)
+    for c, L in enumerate(lists):
+        cx, cy, cz = c % dims[0], (c // dims[0]) % dims[1], c // (dims[0] * dims[1])
+        lo = o + h * np.array([cx, cy, cz]) - 1e-6
+        hi = lo + h + 2e-6
+        for t in L:
+            tl, th = V[tris[t]].min(axis=0), V[tris[t]].max(axis=0)
+            assert np.all(tl <= hi) and np.all(th >= lo)
+    # no missing entries: sample points on each triangle; the (FP64) cell of
+    # each point, when the point is not near a cell face, lists the triangle
+    rng = np.random.default_rng(mi)
+    for t in range(len(tris)):
+        A = V[tris[t]]
+        for _ in range(20):
+            a, b = rng.uniform(0, 1, 2)
+            if a + b > 1:
+                a, b = 1 - a, 1 - b
+            q = A[0] + a * (A[1] - A[0]) + b * (A[2] - A[0])
+            f = (q - o) / h
+            if np.any(np.abs(f - np.rint(f)) < 1e-4):
+                continue
+            cc = np.floor(f).astype(int)
+            c = (cc[2] * dims[1] + cc[1]) * dims[0] + cc[0]
+            assert t in set(lists[c].tolist())
+    # the border cells are empty (origin = min - 1.5h, dims = floor(ext/h) + 4)
+    for c, L in enumerate(lists):
+        cx, cy, cz = c % dims[0], (c // dims[0]) % dims[1], c // (dims[0] * dims[1])
+        if min(cx, cy, cz) == 0 or cx == dims[0] - 1 or cy == dims[1] - 1 or cz == dims[2] - 1:
+            assert len(L) == 0
+
+
+@pytest.mark.parametrize("mi", range(4))
+def test_candidates_contain_every_brute_force_hit(oracle_lib, mi):
+    verts, tris = list(_tiny_meshes())[mi]
+    g = oracle_lib.Grid(verts, tris)
+    V = verts.astype(np.float64)
+    rng = np.random.default_rng(100 + mi)
+    lo, hi = V.min(axis=0) - 0.05, V.max(axis=0) + 0.05
+    nhits = 0
+    for _ in range(1500):
+        S = rng.uniform(lo, hi).astype(np.float32)
+        E = (S + rng.normal(0, 0.03, 3)).astype(np.float32)
+        cand = set(g.candidates_f32(S, E).tolist())
+        for t in range(len(tris)):
+            if oracle_lib.mt(S, E, *V[tris[t]], 1e-7) is not None:
+                nhits += 1
+                assert t in cand
+    assert nhits > 20
+
+
+def test_broad_phase_step_equals_all_pairs_step(oracle_lib):
+    sc = cs.small_collision_scene(n=32, level=2, gap=0.002)
+    cl = oracle_lib.Cloth(sc)
+    grid = oracle_lib.Grid(sc.mesh_verts, sc.mesh_tris)
+    xa, va = xb, vb = sc.init_pos, sc.init_vel
+    contacts = 0
+    for k in range(150):
+        xa, va, ha = oracle_lib.step(cl, xa, va, k, 1, grid, want_hits=True)
+        xb, vb, hb = oracle_lib.step(cl, xb, vb, k, 1, grid, brute=True, want_hits=True)
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ha, hb)
+        contacts += int((ha > 0).sum())
+    assert contacts > 30
+
+
+def test_no_penetration_config1(oracle_lib):
+    # The paper's qualitative claim (Section 4.2): the response keeps the cloth
+    # out of the surface model.  Ray-parity point-in-mesh at several steps.
+    sc = cs.config1()
+    cl = oracle_lib.Cloth(sc)
+    grid = oracle_lib.Grid(sc.mesh_verts, sc.mesh_tris)
+    x, v = sc.init_pos.astype(np.float64), sc.init_vel.astype(np.float64)
+    contacts = 0
+    for blk in range(12):
+        x, v, h = oracle_lib.step(cl, x, v, blk * 25 * sc.substeps, 25 * sc.substeps, grid, want_hits=True)
+        contacts += int((h > 0).sum())
+        inside = ray_parity_inside(x, sc.mesh_verts, sc.mesh_tris)
+        assert not inside.any(), np.nonzero(inside)
+    assert contacts > 50
+
+
+def test_hit_distance_lower_bound_reading(oracle_lib):
+    # A node 5e-8 m above the floor moving down: the literal bound eps < t
+    # (eps = 1e-7) misses the crossing, the default reading 0 < t catches it.
+    S, E = [0.25, 5e-8, 0.75], [0.25, -1e-5, 0.75]
+    V = floor_mesh()[0].astype(np.float64)
+    assert oracle_lib.mt(S, E, V[0], V[2], V[3], 1e-7) is None
+    t = oracle_lib.mt(S, E, V[0], V[2], V[3], 1e-7, t_min=0.0)
+    assert t == pytest.approx(5e-8, rel=1e-6)
+
+
+def test_literal_lower_bound_lets_resting_nodes_through(oracle_lib):
+    # Why the default reading drops eps from the lower bound: with eps < t a
+    # node that ends a substep within eps of the surface crosses it unseen in
+    # the next one, and resting nodes do so within 300 steps of config 1.
+    import dataclasses
+    sc = dataclasses.replace(cs.config1(), mt_t_min=1e-7)
+    cl = oracle_lib.Cloth(sc)
+    grid = oracle_lib.Grid(sc.mesh_verts, sc.mesh_tris)
+    x, v = oracle_lib.step(cl, sc.init_pos, sc.init_vel, 0, 300 * sc.substeps, grid)
+    assert ray_parity_inside(x, sc.mesh_verts, sc.mesh_tris).sum() > 0
