@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Throughput of the cloth step on the paper-scale workload.
+
+Workload: 800x800 grid cloth (640,000 nodes, 3,832,002 structural/shear/bend
+springs), top row pinned, gravity plus a 2 N/kg sinusoidal wind, colliding
+with an 81,920-triangle displaced icosphere (radius 0.25 m) -- the stand-in
+for the paper's 100K-triangle model; dt = 1/1200 s in 4 substeps.  A "step"
+is one cloth_step: 4 fused substep launches (forces, symplectic Euler, grid
+broad phase, MT narrow phase, response) over all nodes.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is whole-job node-steps/s with the state
+resident in HBM (per-step CUDA events on the library's stream, L2 flushed by
+a 256 MiB write before every timed step); `e2e` is the same metric through
+the C ABI with pinned host buffers copied in and out every step.  Under
+torchrun every rank steps its own replica of the cloth (no exchange).
+`--impl reference` times the FP64 CPU oracle on the host on a bounded row
+band of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node-steps/s at 640K nodes + 100K-tri collision; HBM roofline %; adjoint vs fwd"
+UNIT = "node-steps/s"
+BYTES_PER_NODE_SUBSTEP = 48  # read p, v (24 B) + write p, v (24 B), float32 SoA
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "substep_kernel_800x800_l6.txt")
+STEP_SRC = os.path.join(ROOT, "paper_2507_11794_gb300", "csrc", "cloth_step.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the e2e leg (default: --steps, max 1000)")
+    return ap.parse_args()
+
+
+def workload_config(sc):
+    return {
+        "workload": "800x800 grid cloth (640,000 nodes, 3,832,002 springs), top row pinned, gravity + 2 N/kg "
+                    "sinusoidal wind, vs 81,920-triangle displaced icosphere r=0.25 m; dt=1/1200 s, 4 substeps",
+        "nodes": sc.n, "springs": 3832002, "triangles": int(sc.ntris), "substeps_per_step": sc.substeps,
+        "dt": sc.dt, "l2": "flushed (256 MiB write) before every timed step",
+        "parallelism": "replicas",
+    }
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def profile_traffic():
+    """Per-launch DRAM bytes of the substep kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        src_hash = hashlib.sha256(open(STEP_SRC, "rb").read()).hexdigest()[:16]
+        vals = {}
+        for line in open(PROFILE_SUMMARY):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("source_sha256_16") == src_hash and "dram_bytes_per_launch" in vals:
+            return float(vals["dram_bytes_per_launch"])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed loop runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            try:
+                mhz.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        mhz.sort()
+        return {"sm_mhz": mhz[len(mhz) // 2] if mhz else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local, pg
+
+
+def barrier(pg):
+    import torch
+    if pg is not None:
+        if torch.cuda.is_available():
+            pg.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(sc, rows: int, steps: int):
+    """Time the FP64 oracle on the first `rows` rows of the cloth for `steps`
+    steps (1 thread).  Returns (node-steps/s, seconds, nodes)."""
+    import dataclasses
+
+    import numpy as np
+
+    import oracle
+    nx = sc.nx
+    sub = dataclasses.replace(sc, ny=rows, init_pos=sc.init_pos[:rows * nx], init_vel=sc.init_vel[:rows * nx],
+                              pinned=sc.pinned[:rows * nx])
+    cl = oracle.Cloth(sub)
+    grid = oracle.Grid(sub.mesh_verts, sub.mesh_tris)
+    x, v = sub.init_pos, sub.init_vel
+    t0 = time.perf_counter()
+    for s in range(steps):
+        x, v = oracle.step(cl, x, v, s * sub.substeps, sub.substeps, grid)
+    dt = time.perf_counter() - t0
+    assert np.all(np.isfinite(x))
+    return rows * nx * steps / dt, dt, rows * nx
+
+
+def run_reference(args):
+    ws, rank, _, pg = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0, None
+    if rank != 0:
+        return 0
+    import cloth_scenes as cs
+    import oracle
+    oracle.build()
+    sc = cs.config3("l6")
+    # calibrate: one step of a 16-row band, then size the band so the whole
+    # --steps + --warmup run stays within about two minutes
+    _, t16, _ = cpu_oracle_sample(sc, 16, 1)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    rows = int(max(4, min(sc.ny, 16 * budget / max(t16, 1e-6))))
+    cpu_oracle_sample(sc, rows, max(0, min(args.warmup, 3)))
+    val, dt, nodes = cpu_oracle_sample(sc, rows, args.steps)
+    sample = (f"first {rows} rows ({nodes} nodes) of the 800x800 cloth with the full 81,920-triangle mesh, "
+              f"{args.steps} steps x 4 substeps from the initial state, FP64 oracle, 1 thread")
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(sc), "impl": "reference",
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import cloth_scenes as cs
+    import paper_2507_11794_gb300 as P
+    from paper_2507_11794_gb300 import build as B
+
+    ws, rank, local, pg = dist_setup()
+    if rank == 0 or pg is None:
+        B.build()
+    barrier(pg)
+    sc = cs.config3("l6")
+    N, SUB = sc.n, sc.substeps
+    stream = torch.cuda.current_stream()
+    cl = P.Cloth(sc, stream=int(stream.cuda_stream))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        cl.step(1)
+    cl.sync()
+    cl.set_state(sc.init_pos, sc.init_vel)  # timed run starts from the workload's initial state
+    cl.sync()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(pg)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            cl.step(1)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    barrier(pg)
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    pos, vel = cl.read()
+    assert np.all(np.isfinite(pos)) and np.all(np.isfinite(vel))
+    t = max_over_ranks(pg, dev_ms / 1e3)
+    value = ws * N * args.steps / t
+    launches = SUB * args.steps
+    avg_launch_s = (dev_ms / 1e3) / launches
+
+    # end to end through the C ABI: pinned host state in, step, state out
+    ke = args.e2e_steps or min(args.steps, 1000)
+    hp = torch.empty((N, 3), dtype=torch.float32, pin_memory=True).numpy()
+    hv = torch.empty((N, 3), dtype=torch.float32, pin_memory=True).numpy()
+    hp[:] = sc.init_pos
+    hv[:] = sc.init_vel
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(ke):
+        cl.set_state(hp, hv)
+        cl.step(1)
+        cl.read(out_pos=hp, out_vel=hv)
+    e2e_t = max_over_ranks(pg, time.perf_counter() - e0)
+    e2e_val = ws * N * ke / e2e_t
+
+    cl.close()
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
+    peak_src = "measured" if peaks and "hbm_gbs" in peaks else "fallback"
+    achieved = BYTES_PER_NODE_SUBSTEP * N / avg_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profile_traffic(), "peak_source": peak_src,
+                "kernel": "substep_kernel<MESH=true>", "algorithmic_bytes_per_launch": BYTES_PER_NODE_SUBSTEP * N,
+                "avg_launch_us": avg_launch_s * 1e6}
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        rows = 40
+        val, dt, nodes = cpu_oracle_sample(sc, rows, 12)
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {rows} rows ({nodes} nodes) of the same cloth with the full mesh, 12 steps x 4 "
+                         f"substeps from the initial state ({dt:.1f} s, FP64, 1 thread)"}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": workload_config(sc),
+           "roofline": roofline, "cpu_baseline": cpu,
+           "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 12 * N,
+                   "d2h_bytes_per_step": 2 * 12 * N, "steps": ke},
+           "gpu_launches": launches, "clocks": clocks.summary(),
+           "wall_s_timed_loop": wall}
+    print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * cloth.h -- C ABI of the GB300 mass-spring cloth library (libcloth.so).
+ *
+ * The library steps the per-timestep hot path of the mass-spring cloth of
+ * "Real-Time Cloth Simulation Using WebGPU" (arXiv 2507.11794) on one GPU:
+ *   - spring + damping forces of the structural, shear and bend springs of a
+ *     grid cloth (Section 3 "Methodology"; Algorithm 1, Hooke's law with
+ *     damping along the spring), gathered per node in a fixed order;
+ *   - "the Euler method" with spring force, gravity and external force
+ *     (Section 3), read as symplectic Euler, with pinned nodes (the hanging
+ *     cloth of Section 4.1);
+ *   - collision with a static ("baked", Section 4.2) triangle surface model:
+ *     a uniform-grid broad phase (not in the paper, which tests all pairs) and
+ *     the extended Moller-Trumbore test on each node's substep path
+ *     (Section 3, "Extended Moller-Trumbore Process");
+ *   - the collision response of Section 3 and Algorithm 2: on K > 0 hits the
+ *     node restarts from its previous position plus the average response
+ *     (1/K) sum_k max(t_k - delta, 0) * r, and its velocity is scaled by
+ *     `restitution` (Algorithm 2: -0.5).
+ *
+ * Conventions
+ *   - Every call returns 0 (CLOTH_OK) or a negative CLOTH_ERR_* code; nothing
+ *     throws across the ABI.  cloth_last_error() returns a message for the
+ *     calling thread's most recent failure.
+ *   - Ownership: the library owns all device memory it allocates; callers own
+ *     every host buffer they pass, which is only read during the call.
+ *   - Layout of host node arrays: N = nx*ny nodes, node id = row*nx + col;
+ *     positions and velocities are AoS float32 [N][3].
+ *   - Streams: all GPU work of a handle runs on the stream given at create
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *     cloth_step is asynchronous; cloth_read and cloth_sync synchronise the
+ *     stream.  Errors raised by earlier asynchronous work (a non-finite
+ *     state, a CUDA fault) are reported by the next synchronising call.
+ *   - After CLOTH_ERR_CUDA a handle is unusable: every call but
+ *     cloth_destroy returns CLOTH_ERR_STATE.
+ *   - Handles are not thread-safe; distinct handles may be used from
+ *     distinct threads.
+ */
+#ifndef CLOTH_H
+#define CLOTH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CLOTH_OK = 0,
+    CLOTH_ERR_INVALID_ARG = -1, /* bad pointer, size or parameter */
+    CLOTH_ERR_OOM = -2,         /* device or host allocation failed */
+    CLOTH_ERR_CUDA = -3,        /* a CUDA call failed; the handle is now unusable */
+    CLOTH_ERR_NONFINITE = -4,   /* a position or velocity became NaN/Inf */
+    CLOTH_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    CLOTH_ERR_BAD_MESH = -6,    /* triangle index out of range, bad sizes */
+    CLOTH_ERR_STATE = -7        /* handle unusable after an earlier CUDA error */
+};
+
+/* Flags of ClothDesc.flags */
+#define CLOTH_FLAG_NO_GRAPH 1u /* launch substeps one by one instead of a CUDA graph */
+
+/* Sinusoidal external acceleration field (N/kg) added to gravity:
+ *   w(X0, t) = amp * dir * sin(2*pi*freq*t + kappa*(udir . X0) + phase),
+ * X0 the node's rest position, t = k*dt_s the start time of substep k.
+ * amp = 0 disables it. */
+typedef struct ClothWind {
+    float amp;
+    float dir[3];
+    float udir[3];
+    float freq;
+    float kappa;
+    float phase;
+} ClothWind;
+
+/* Problem statement of one cloth (caller-owned; copied by cloth_create).
+ * The paper's inputs: springs with stiffness, rest length and damping
+ * (Algorithm 1), node positions/velocities (Algorithm 2), masses, gravity,
+ * external force and the Euler time step (Section 3). */
+typedef struct ClothDesc {
+    int32_t nx, ny;          /* grid resolution in nodes (>= 1 each); N = nx*ny */
+    float origin[3];         /* rest position of node (0,0) */
+    float du[3], dv[3];      /* rest offsets between columns / rows:
+                                X0(row,col) = origin + col*du + row*dv; rest
+                                lengths come from this flat grid */
+    float total_mass;        /* kg, spread uniformly: m = total_mass / N */
+    float ks[3], kd[3];      /* per type (structural, shear, bend): N/m, N*s/m */
+    const float *ks_spring;  /* optional host array of S floats in canonical
+                                spring order (below), overriding ks[]; NULL = off */
+    const float *kd_spring;  /* optional, likewise for kd */
+    const float *init_pos;   /* optional host [N][3]; NULL = the flat grid X0 */
+    const float *init_vel;   /* optional host [N][3]; NULL = 0 */
+    const uint8_t *pinned;   /* optional host [N], nonzero = pinned; NULL = none */
+    float gravity[3];        /* m/s^2 */
+    float dt;                /* time advanced by one cloth_step (s) */
+    int32_t substeps;        /* substeps per cloth_step (>= 1); dt_s = dt/substeps */
+    float contact_offset;    /* delta (m): a hit stops the node delta before it */
+    float mt_eps;            /* epsilon of the extended MT parallel test |a| < eps */
+    float mt_t_min;          /* hits need mt_t_min < t < |d| (paper text: eps) */
+    float restitution;       /* velocity factor on contact (Algorithm 2: -0.5) */
+    ClothWind wind;
+    uint32_t flags;          /* CLOTH_FLAG_* */
+} ClothDesc;
+
+/* Canonical spring order (for ks_spring / kd_spring): nodes in row-major
+ * order, each emitting its springs towards (drow,dcol) = (0,+1), (+1,0),
+ * (+1,+1), (+1,-1), (0,+2), (+2,0) when the other end lies in the grid.
+ * Types: the first two structural, the next two shear, the last two bend.
+ * S = 2*nx*ny - nx - ny + 2*(nx-1)*(ny-1) + nx*(ny-2)^+ + ny*(nx-2)^+. */
+
+typedef struct ClothHandle ClothHandle;
+
+/* Create a cloth on the current CUDA device.  desc is validated (sizes,
+ * finiteness, dt > 0, substeps >= 1, total_mass > 0) and copied with its
+ * arrays; stream is the cudaStream_t all work of the handle runs on.
+ * Returns CLOTH_ERR_INVALID_ARG, CLOTH_ERR_OOM or CLOTH_ERR_CUDA on failure
+ * (*out is then NULL). */
+int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out);
+
+/* Set (or with ntris = 0 clear) the static surface model: host arrays of
+ * nverts*3 float32 vertex coordinates and ntris*3 int32 vertex indices,
+ * copied.  Builds the uniform grid on the device (counting sort of the
+ * (cell, triangle) pairs).  Indices outside [0, nverts) or non-finite
+ * vertices return CLOTH_ERR_BAD_MESH and leave the previous mesh in place.
+ * Synchronises the stream. */
+int cloth_set_mesh(ClothHandle *h, const float *verts, int32_t nverts, const int32_t *tris, int32_t ntris);
+
+/* Enqueue nsteps steps (nsteps * substeps substeps) on the stream. */
+int cloth_step(ClothHandle *h, int32_t nsteps);
+
+/* Copy the current state to caller-owned host [N][3] arrays (either may be
+ * NULL).  Synchronises; returns CLOTH_ERR_NONFINITE if the state has become
+ * non-finite since create/set_state (the arrays are still written). */
+int cloth_read(ClothHandle *h, float *pos_out, float *vel_out);
+
+/* Release everything the handle owns.  NULL-safe.  Synchronises the stream. */
+void cloth_destroy(ClothHandle *h);
+
+/* ---- extras --------------------------------------------------------- */
+
+/* Overwrite the current state from host [N][3] arrays (NULL keeps that
+ * part) and clear the non-finite flag.  Asynchronous for pinned host memory
+ * (the host arrays must stay valid until the stream reaches the copy);
+ * pageable memory is copied before return. */
+int cloth_set_state(ClothHandle *h, const float *pos, const float *vel);
+
+/* Wait for the handle's stream and report device-side error flags. */
+int cloth_sync(ClothHandle *h);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char *cloth_last_error(void);
+
+typedef struct ClothInfo {
+    int32_t nx, ny, n;
+    int32_t substeps;
+    int64_t substeps_done;     /* substeps enqueued since create */
+    int64_t plane_stride;      /* floats between consecutive SoA planes */
+    float *pos_planes[3];      /* device pointers of the current x,y,z planes */
+    float *vel_planes[3];      /* (valid until the next cloth_step/set_state) */
+    int32_t ntris;
+    int32_t grid_dims[3];
+    float grid_origin[3];
+    float grid_h, grid_inv;
+    int64_t grid_entries;
+    int32_t has_per_spring;
+} ClothInfo;
+
+/* Sizes, grid parameters and device pointers of the current SoA state. */
+int cloth_get_info(ClothHandle *h, ClothInfo *info);
+
+/* Copy the uniform grid to host arrays: cell_start [cells+1] and tri_ids
+ * [grid_entries] (each cell's ids ascending).  Synchronises. */
+int cloth_get_grid(ClothHandle *h, int32_t *cell_start, int32_t *tri_ids);
+
+/* Broad-phase query on the device for nseg float32 segments S->E (host
+ * [nseg][3] arrays): counts[i] = number of distinct candidate triangles of
+ * segment i (the triangles listed in the grid cells overlapped by the
+ * segment's AABB); ids receives up to cap ids per segment at ids[i*cap ..],
+ * in no particular order.  Synchronises. */
+int cloth_query_candidates(ClothHandle *h, const float *S, const float *E, int32_t nseg,
+                           int32_t *counts, int32_t *ids, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLOTH_H */

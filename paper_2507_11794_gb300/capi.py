@@ -1,0 +1,203 @@
+"""ctypes binding of libcloth.so (the C ABI of include/cloth.h).
+
+Argument marshalling only: every step of the cloth path runs in the CUDA
+kernels of the library.  The functions keep the C names (cloth_create,
+cloth_set_mesh, cloth_step, cloth_read, cloth_destroy, ...) and raise
+``ClothError`` on a negative status.  If the library is missing or cannot be
+loaded, ``lib()`` raises: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcloth.so")
+
+CLOTH_OK = 0
+CLOTH_ERR_INVALID_ARG = -1
+CLOTH_ERR_OOM = -2
+CLOTH_ERR_CUDA = -3
+CLOTH_ERR_NONFINITE = -4
+CLOTH_ERR_TIMEOUT = -5
+CLOTH_ERR_BAD_MESH = -6
+CLOTH_ERR_STATE = -7
+CLOTH_FLAG_NO_GRAPH = 1
+
+_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT",
+          -6: "BAD_MESH", -7: "STATE"}
+
+# Every symbol include/cloth.h declares (checked by the CPU test-suite).
+EXPORTS = ("cloth_create", "cloth_set_mesh", "cloth_step", "cloth_read", "cloth_destroy",
+           "cloth_set_state", "cloth_sync", "cloth_last_error", "cloth_get_info", "cloth_get_grid",
+           "cloth_query_candidates")
+
+
+class ClothError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"CLOTH_ERR_{_NAMES.get(code, code)} ({code}): {msg}")
+        self.code = code
+
+
+class ClothWind(C.Structure):
+    _fields_ = [("amp", C.c_float), ("dir", C.c_float * 3), ("udir", C.c_float * 3), ("freq", C.c_float),
+                ("kappa", C.c_float), ("phase", C.c_float)]
+
+
+class ClothDesc(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32),
+        ("origin", C.c_float * 3), ("du", C.c_float * 3), ("dv", C.c_float * 3),
+        ("total_mass", C.c_float),
+        ("ks", C.c_float * 3), ("kd", C.c_float * 3),
+        ("ks_spring", C.POINTER(C.c_float)), ("kd_spring", C.POINTER(C.c_float)),
+        ("init_pos", C.POINTER(C.c_float)), ("init_vel", C.POINTER(C.c_float)),
+        ("pinned", C.POINTER(C.c_uint8)),
+        ("gravity", C.c_float * 3),
+        ("dt", C.c_float), ("substeps", C.c_int32),
+        ("contact_offset", C.c_float), ("mt_eps", C.c_float), ("mt_t_min", C.c_float),
+        ("restitution", C.c_float),
+        ("wind", ClothWind),
+        ("flags", C.c_uint32),
+    ]
+
+
+class ClothInfo(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("n", C.c_int32), ("substeps", C.c_int32),
+        ("substeps_done", C.c_int64), ("plane_stride", C.c_int64),
+        ("pos_planes", C.c_void_p * 3), ("vel_planes", C.c_void_p * 3),
+        ("ntris", C.c_int32), ("grid_dims", C.c_int32 * 3), ("grid_origin", C.c_float * 3),
+        ("grid_h", C.c_float), ("grid_inv", C.c_float), ("grid_entries", C.c_int64),
+        ("has_per_spring", C.c_int32),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libcloth.so (built by paper_2507_11794_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2507_11794_gb300.build.build() "
+                              "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        fp, ip, u8 = C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_uint8)
+        H = C.c_void_p
+        L.cloth_create.argtypes = [C.POINTER(ClothDesc), C.c_void_p, C.POINTER(C.c_void_p)]
+        L.cloth_set_mesh.argtypes = [H, fp, C.c_int32, ip, C.c_int32]
+        L.cloth_step.argtypes = [H, C.c_int32]
+        L.cloth_read.argtypes = [H, fp, fp]
+        L.cloth_destroy.argtypes = [H]
+        L.cloth_destroy.restype = None
+        L.cloth_set_state.argtypes = [H, fp, fp]
+        L.cloth_sync.argtypes = [H]
+        L.cloth_last_error.argtypes = []
+        L.cloth_last_error.restype = C.c_char_p
+        L.cloth_get_info.argtypes = [H, C.POINTER(ClothInfo)]
+        L.cloth_get_grid.argtypes = [H, ip, ip]
+        L.cloth_query_candidates.argtypes = [H, fp, fp, C.c_int32, ip, ip, C.c_int32]
+        for name in EXPORTS:
+            f = getattr(L, name)
+            if name not in ("cloth_destroy", "cloth_last_error"):
+                f.restype = C.c_int
+        _lib = L
+        return L
+
+
+def check(rc: int):
+    if rc < 0:
+        raise ClothError(rc, lib().cloth_last_error().decode(errors="replace"))
+    return rc
+
+
+def _fp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _ip(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def f32(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a if shape is None else a.reshape(shape)
+
+
+# ---------------------------------------------------------------- C names
+
+def cloth_create(desc: ClothDesc, stream: int = 0) -> int:
+    h = C.c_void_p()
+    check(lib().cloth_create(C.byref(desc), C.c_void_p(stream), C.byref(h)))
+    return h.value
+
+
+def cloth_set_mesh(h: int, verts, tris):
+    v = None if verts is None else f32(verts, (-1, 3))
+    t = None if tris is None else np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+    nv = 0 if v is None else len(v)
+    nt = 0 if t is None else len(t)
+    check(lib().cloth_set_mesh(h, _fp(v), nv, _ip(t), nt))
+
+
+def cloth_step(h: int, nsteps: int):
+    check(lib().cloth_step(h, int(nsteps)))
+
+
+def cloth_read(h: int, n: int, pos=True, vel=True, out_pos=None, out_vel=None):
+    """Returns (pos, vel) as float32 (N,3) arrays (None for a part not read)."""
+    p = (out_pos if out_pos is not None else np.empty((n, 3), np.float32)) if pos else None
+    v = (out_vel if out_vel is not None else np.empty((n, 3), np.float32)) if vel else None
+    check(lib().cloth_read(h, _fp(p), _fp(v)))
+    return p, v
+
+
+def cloth_set_state(h: int, pos=None, vel=None):
+    check(lib().cloth_set_state(h, _fp(f32(pos)), _fp(f32(vel))))
+
+
+def cloth_sync(h: int):
+    check(lib().cloth_sync(h))
+
+
+def cloth_destroy(h: int):
+    if h:
+        lib().cloth_destroy(h)
+
+
+def cloth_get_info(h: int) -> ClothInfo:
+    info = ClothInfo()
+    check(lib().cloth_get_info(h, C.byref(info)))
+    return info
+
+
+def cloth_get_grid(h: int):
+    info = cloth_get_info(h)
+    nc = int(info.grid_dims[0]) * int(info.grid_dims[1]) * int(info.grid_dims[2])
+    cs = np.empty(nc + 1, np.int32)
+    ids = np.empty(max(int(info.grid_entries), 1), np.int32)
+    check(lib().cloth_get_grid(h, _ip(cs), _ip(ids)))
+    return cs, ids[:int(info.grid_entries)]
+
+
+def cloth_query_candidates(h: int, S, E, cap: int = 64):
+    S = f32(S, (-1, 3))
+    E = f32(E, (-1, 3))
+    n = len(S)
+    while True:
+        counts = np.empty(n, np.int32)
+        ids = np.empty((n, cap), np.int32)
+        check(lib().cloth_query_candidates(h, _fp(S), _fp(E), n, _ip(counts), _ip(ids), cap))
+        if n == 0 or counts.max() <= cap:
+            return counts, ids
+        cap = int(counts.max())

@@ -1,0 +1,554 @@
+// Host side of the C ABI declared in include/cloth.h: handle lifetime,
+// device memory, validation, CUDA-graph replay of substep blocks and error
+// reporting.  No exception crosses the ABI.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "cloth_internal.h"
+
+struct ClothHandle {
+    ClothDesc desc;  // array pointers cleared after the copy
+    int n = 0;
+    long long stride = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    float *state = nullptr;  // 2 buffers x 6 planes x stride
+    uint32_t *pin_bits = nullptr;
+    float *ks_slot = nullptr, *kd_slot = nullptr;
+    DevCtrl *ctrl = nullptr;
+    float *staging = nullptr;  // 6*n floats for AoS transfers
+    DevGrid grid{};
+    bool has_mesh = false;
+    StepParams params{};
+    cudaGraphExec_t graph = nullptr;
+    long long substeps_done = 0;
+    bool dead = false;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(ClothHandle *h, cudaError_t e, const char *what)
+{
+    if (h) h->dead = true;
+    return fail(CLOTH_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CTRY(h, call, what)                                  \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+// Makes the handle's device current for the scope of one API call.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceScope()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite3(const float *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+long long spring_count(long long nx, long long ny)
+{
+    long long s = nx * (ny - 1) + ny * (nx - 1) + 2 * (nx - 1) * (ny - 1);
+    s += nx * (ny > 2 ? ny - 2 : 0) + ny * (nx > 2 ? nx - 2 : 0);
+    return s;
+}
+
+const int kDR[CLOTH_NDIR] = {0, 1, 1, 1, 0, 2};
+const int kDC[CLOTH_NDIR] = {1, 0, 1, -1, 2, 0};
+
+void free_all(ClothHandle *h)
+{
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    grid_free(&h->grid);
+    cudaFree(h->state);
+    cudaFree(h->pin_bits);
+    cudaFree(h->ks_slot);
+    cudaFree(h->kd_slot);
+    cudaFree(h->ctrl);
+    cudaFree(h->staging);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->state = nullptr;
+    h->pin_bits = nullptr;
+    h->ks_slot = h->kd_slot = nullptr;
+    h->ctrl = nullptr;
+    h->staging = nullptr;
+    h->cap_stream = nullptr;
+}
+
+void fill_params(ClothHandle *h)
+{
+    const ClothDesc &d = h->desc;
+    StepParams &p = h->params;
+    p.nx = d.nx;
+    p.ny = d.ny;
+    p.n = h->n;
+    p.stride = h->stride;
+    p.state0 = h->state;
+    p.state1 = h->state + 6 * h->stride;
+    p.pin_bits = h->pin_bits;
+    p.ks_slot = h->ks_slot;
+    p.kd_slot = h->kd_slot;
+    for (int a = 0; a < 3; a++) {
+        p.ks[a] = d.ks[a];
+        p.kd[a] = d.kd[a];
+        p.g[a] = d.gravity[a];
+        p.w_dir[a] = d.wind.dir[a];
+    }
+    // rest lengths of the six directions from the flat grid, in double
+    for (int k = 0; k < CLOTH_NDIR; k++) {
+        double l2 = 0.0;
+        for (int a = 0; a < 3; a++) {
+            const double e = (double)kDC[k] * d.du[a] + (double)kDR[k] * d.dv[a];
+            l2 += e * e;
+        }
+        p.L0[k] = (float)sqrt(l2);
+    }
+    const double dt_s = (double)d.dt / (double)d.substeps;
+    p.dt = (float)dt_s;
+    p.inv_mass = (float)((double)h->n / (double)d.total_mass);
+    p.has_wind = d.wind.amp != 0.0f;
+    p.w_amp = d.wind.amp;
+    const double two_pi = 6.283185307179586;
+    p.w_omega = two_pi * (double)d.wind.freq * dt_s;
+    double k0 = 0.0, kc = 0.0, kr = 0.0;
+    for (int a = 0; a < 3; a++) {
+        k0 += (double)d.wind.udir[a] * d.origin[a];
+        kc += (double)d.wind.udir[a] * d.du[a];
+        kr += (double)d.wind.udir[a] * d.dv[a];
+    }
+    p.w_phase0 = fmod((double)d.wind.phase + (double)d.wind.kappa * k0, two_pi);
+    p.w_kc = (float)((double)d.wind.kappa * kc);
+    p.w_kr = (float)((double)d.wind.kappa * kr);
+    p.has_mesh = h->has_mesh;
+    p.tri = h->grid.tri;
+    p.cell_start = h->grid.cell_start;
+    p.tri_ids = h->grid.tri_ids;
+    for (int a = 0; a < 3; a++) {
+        p.go[a] = h->grid.origin[a];
+        p.gd[a] = h->grid.dims[a];
+    }
+    p.ginv = h->grid.inv;
+    p.delta = d.contact_offset;
+    p.eps = d.mt_eps;
+    p.tmin = d.mt_t_min;
+    p.restitution = d.restitution;
+    p.ctrl = h->ctrl;
+}
+
+void invalidate_graph(ClothHandle *h)
+{
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+}
+
+// Capture one step (desc.substeps launches) as a graph on a private stream.
+cudaError_t ensure_graph(ClothHandle *h)
+{
+    if (h->graph) return cudaSuccess;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int s = 0; s < h->desc.substeps && le == cudaSuccess; s++) le = launch_substep(h->params, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+int check_handle(ClothHandle *h)
+{
+    if (!h) return fail(CLOTH_ERR_INVALID_ARG, "null handle");
+    if (h->dead) return fail(CLOTH_ERR_STATE, "handle unusable after an earlier CUDA error");
+    return CLOTH_OK;
+}
+
+int read_flags(ClothHandle *h, unsigned *flags)
+{
+    CTRY(h, cudaMemcpyAsync(flags, &h->ctrl->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream),
+         "read device flags");
+    CTRY(h, cudaStreamSynchronize(h->stream), "synchronize");
+    return CLOTH_OK;
+}
+
+int flags_status(unsigned flags)
+{
+    if (flags & CTRL_FLAG_TIMEOUT) return fail(CLOTH_ERR_TIMEOUT, "a device-side wait timed out");
+    if (flags & CTRL_FLAG_NONFINITE) return fail(CLOTH_ERR_NONFINITE, "state became non-finite");
+    return CLOTH_OK;
+}
+
+// Host array -> device buffer (synchronous for pageable memory).
+cudaError_t upload(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cloth_last_error(void) { return g_err; }
+
+int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
+{
+    if (!out) return fail(CLOTH_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(CLOTH_ERR_INVALID_ARG, "desc is NULL");
+    const ClothDesc &d = *desc;
+    if (d.nx < 1 || d.ny < 1) return fail(CLOTH_ERR_INVALID_ARG, "nx, ny must be >= 1");
+    const long long N = (long long)d.nx * d.ny;
+    if (N > (1ll << 30)) return fail(CLOTH_ERR_INVALID_ARG, "too many nodes (%lld)", N);
+    if (d.substeps < 1) return fail(CLOTH_ERR_INVALID_ARG, "substeps must be >= 1");
+    if (!(d.dt > 0.0f) || !isfinite(d.dt)) return fail(CLOTH_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (!(d.total_mass > 0.0f) || !isfinite(d.total_mass))
+        return fail(CLOTH_ERR_INVALID_ARG, "total_mass must be finite and > 0");
+    if (!finite3(d.origin) || !finite3(d.du) || !finite3(d.dv) || !finite3(d.ks) || !finite3(d.kd) ||
+        !finite3(d.gravity) || !finite3(d.wind.dir) || !finite3(d.wind.udir) || !isfinite(d.wind.amp) ||
+        !isfinite(d.wind.freq) || !isfinite(d.wind.kappa) || !isfinite(d.wind.phase) || !isfinite(d.contact_offset) ||
+        !isfinite(d.mt_eps) || !isfinite(d.mt_t_min) || !isfinite(d.restitution))
+        return fail(CLOTH_ERR_INVALID_ARG, "non-finite parameter in desc");
+    const long long S = spring_count(d.nx, d.ny);
+    if (d.init_pos)
+        for (long long i = 0; i < 3 * N; i++)
+            if (!isfinite(d.init_pos[i])) return fail(CLOTH_ERR_INVALID_ARG, "non-finite init_pos[%lld]", i);
+    if (d.init_vel)
+        for (long long i = 0; i < 3 * N; i++)
+            if (!isfinite(d.init_vel[i])) return fail(CLOTH_ERR_INVALID_ARG, "non-finite init_vel[%lld]", i);
+    if (d.ks_spring)
+        for (long long i = 0; i < S; i++)
+            if (!isfinite(d.ks_spring[i])) return fail(CLOTH_ERR_INVALID_ARG, "non-finite ks_spring[%lld]", i);
+    if (d.kd_spring)
+        for (long long i = 0; i < S; i++)
+            if (!isfinite(d.kd_spring[i])) return fail(CLOTH_ERR_INVALID_ARG, "non-finite kd_spring[%lld]", i);
+
+    ClothHandle *h = new (std::nothrow) ClothHandle();
+    if (!h) return fail(CLOTH_ERR_OOM, "host allocation failed");
+    h->desc = d;
+    h->desc.ks_spring = h->desc.kd_spring = nullptr;
+    h->desc.init_pos = h->desc.init_vel = nullptr;
+    h->desc.pinned = nullptr;
+    h->n = (int)N;
+    h->stride = (N + 63) / 64 * 64;  // 256-byte aligned planes
+    h->stream = (cudaStream_t)stream;
+    cudaGetDevice(&h->device);
+
+    int rc = CLOTH_OK;
+    cudaError_t e = cudaSuccess;
+    try {
+    do {
+        if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&h->state, sizeof(float) * 12 * (size_t)h->stride)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&h->ctrl, sizeof(DevCtrl))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&h->staging, sizeof(float) * 6 * (size_t)N)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(h->ctrl, 0, sizeof(DevCtrl), h->stream)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(h->state, 0, sizeof(float) * 12 * (size_t)h->stride, h->stream)) != cudaSuccess)
+            break;
+        // initial state: given arrays, else the flat grid (computed in double) at rest
+        std::vector<float> init(6 * (size_t)N, 0.0f);
+        for (long long i = 0; i < N; i++) {
+            const long long r = i / d.nx, c = i % d.nx;
+            for (int a = 0; a < 3; a++) {
+                init[3 * i + a] = d.init_pos ? d.init_pos[3 * i + a]
+                                             : (float)((double)d.origin[a] + (double)c * d.du[a] + (double)r * d.dv[a]);
+                init[3 * N + 3 * i + a] = d.init_vel ? d.init_vel[3 * i + a] : 0.0f;
+            }
+        }
+        if ((e = upload(h->staging, init.data(), sizeof(float) * 6 * (size_t)N, h->stream)) != cudaSuccess) break;
+        if ((e = launch_aos_to_soa(h->staging, h->staging + 3 * N, h->state, h->state + 6 * h->stride, h->stride,
+                                   (int)N, h->ctrl, h->stream)) != cudaSuccess)
+            break;
+        if (d.pinned) {
+            std::vector<uint32_t> bits((size_t)(N + 31) / 32, 0u);
+            bool any = false;
+            for (long long i = 0; i < N; i++)
+                if (d.pinned[i]) {
+                    bits[(size_t)(i >> 5)] |= 1u << (i & 31);
+                    any = true;
+                }
+            if (any) {
+                if ((e = cudaMalloc(&h->pin_bits, sizeof(uint32_t) * bits.size())) != cudaSuccess) break;
+                if ((e = upload(h->pin_bits, bits.data(), sizeof(uint32_t) * bits.size(), h->stream)) != cudaSuccess)
+                    break;
+            }
+        }
+        if (d.ks_spring || d.kd_spring) {
+            // canonical order -> [direction][owner node] slots
+            std::vector<float> ks(6 * (size_t)h->stride, 0.0f), kd(6 * (size_t)h->stride, 0.0f);
+            const int type[CLOTH_NDIR] = {0, 0, 1, 1, 2, 2};
+            long long s = 0;
+            for (long long r = 0; r < d.ny; r++)
+                for (long long c = 0; c < d.nx; c++)
+                    for (int k = 0; k < CLOTH_NDIR; k++) {
+                        const long long r2 = r + kDR[k], c2 = c + kDC[k];
+                        if (r2 < 0 || r2 >= d.ny || c2 < 0 || c2 >= d.nx) continue;
+                        const size_t slot = (size_t)k * h->stride + (size_t)(r * d.nx + c);
+                        ks[slot] = d.ks_spring ? d.ks_spring[s] : d.ks[type[k]];
+                        kd[slot] = d.kd_spring ? d.kd_spring[s] : d.kd[type[k]];
+                        s++;
+                    }
+            if ((e = cudaMalloc(&h->ks_slot, sizeof(float) * ks.size())) != cudaSuccess) break;
+            if ((e = cudaMalloc(&h->kd_slot, sizeof(float) * kd.size())) != cudaSuccess) break;
+            if ((e = upload(h->ks_slot, ks.data(), sizeof(float) * ks.size(), h->stream)) != cudaSuccess) break;
+            if ((e = upload(h->kd_slot, kd.data(), sizeof(float) * kd.size(), h->stream)) != cudaSuccess) break;
+        }
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) break;
+    } while (0);
+    } catch (...) {
+        cudaStreamSynchronize(h->stream);
+        free_all(h);
+        delete h;
+        return fail(CLOTH_ERR_OOM, "host allocation failed");
+    }
+    if (e != cudaSuccess) {
+        rc = (e == cudaErrorMemoryAllocation) ? fail(CLOTH_ERR_OOM, "device allocation failed: %s", cudaGetErrorString(e))
+                                              : cuda_fail(nullptr, e, "cloth_create");
+        free_all(h);
+        delete h;
+        cudaGetLastError();
+        return rc;
+    }
+    fill_params(h);
+    *out = h;
+    return CLOTH_OK;
+}
+
+int cloth_set_mesh(ClothHandle *h, const float *verts, int32_t nverts, const int32_t *tris, int32_t ntris)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (ntris < 0 || nverts < 0) return fail(CLOTH_ERR_BAD_MESH, "negative mesh size");
+    if (ntris > 0 && (!verts || !tris || nverts < 1)) return fail(CLOTH_ERR_BAD_MESH, "missing mesh arrays");
+    for (long long i = 0; i < 3 * (long long)ntris; i++)
+        if (tris[i] < 0 || tris[i] >= nverts)
+            return fail(CLOTH_ERR_BAD_MESH, "triangle index %d at %lld out of range [0, %d)", tris[i], i, nverts);
+    for (long long i = 0; i < 3 * (long long)nverts && ntris > 0; i++)
+        if (!isfinite(verts[i])) return fail(CLOTH_ERR_BAD_MESH, "non-finite vertex coordinate at %lld", i);
+    DeviceScope ds(h->device);
+    CTRY(h, cudaStreamSynchronize(h->stream), "synchronize");
+    DevGrid g{};
+    if (ntris > 0) {
+        if (grid_params(verts, tris, ntris, &g.h, g.origin, g.dims, &g.inv) != 0)
+            return fail(CLOTH_ERR_BAD_MESH, "grid parameters");
+        float *dv = nullptr;
+        int *dt = nullptr;
+        cudaError_t e = cudaMalloc(&dv, sizeof(float) * 3 * (size_t)nverts);
+        if (e == cudaSuccess) e = cudaMalloc(&dt, sizeof(int) * 3 * (size_t)ntris);
+        if (e == cudaSuccess) e = upload(dv, verts, sizeof(float) * 3 * (size_t)nverts, h->stream);
+        if (e == cudaSuccess) e = upload(dt, tris, sizeof(int) * 3 * (size_t)ntris, h->stream);
+        if (e == cudaSuccess) e = grid_build(dv, dt, ntris, &g, h->stream);
+        cudaFree(dv);
+        cudaFree(dt);
+        if (e == cudaErrorInvalidValue) {
+            cudaGetLastError();
+            return fail(CLOTH_ERR_BAD_MESH, "mesh needs more than 2^31 grid entries");
+        }
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return fail(CLOTH_ERR_OOM, "device allocation failed while building the grid");
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "grid build");
+    }
+    grid_free(&h->grid);
+    h->grid = g;
+    h->has_mesh = ntris > 0;
+    fill_params(h);
+    invalidate_graph(h);
+    return CLOTH_OK;
+}
+
+int cloth_step(ClothHandle *h, int32_t nsteps)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(CLOTH_ERR_INVALID_ARG, "nsteps < 0");
+    if (nsteps == 0) return CLOTH_OK;
+    DeviceScope ds(h->device);
+    if (h->desc.flags & CLOTH_FLAG_NO_GRAPH) {
+        for (int s = 0; s < nsteps; s++)
+            for (int j = 0; j < h->desc.substeps; j++) CTRY(h, launch_substep(h->params, h->stream), "substep launch");
+    } else {
+        CTRY(h, ensure_graph(h), "graph capture");
+        for (int s = 0; s < nsteps; s++) CTRY(h, cudaGraphLaunch(h->graph, h->stream), "graph launch");
+    }
+    h->substeps_done += (long long)nsteps * h->desc.substeps;
+    return CLOTH_OK;
+}
+
+int cloth_read(ClothHandle *h, float *pos_out, float *vel_out)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    DeviceScope ds(h->device);
+    const long long N = h->n;
+    unsigned flags = 0;
+    if (pos_out || vel_out) {
+        CTRY(h, launch_soa_to_aos(h->state, h->state + 6 * h->stride, h->stride, h->n, h->ctrl,
+                                  pos_out ? h->staging : nullptr, vel_out ? h->staging + 3 * N : nullptr, h->stream),
+             "state gather");
+        if (pos_out)
+            CTRY(h, cudaMemcpyAsync(pos_out, h->staging, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->stream),
+                 "copy positions");
+        if (vel_out)
+            CTRY(h, cudaMemcpyAsync(vel_out, h->staging + 3 * N, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost,
+                                    h->stream),
+                 "copy velocities");
+    }
+    rc = read_flags(h, &flags);
+    if (rc) return rc;
+    return flags_status(flags);
+}
+
+int cloth_set_state(ClothHandle *h, const float *pos, const float *vel)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!pos && !vel) return CLOTH_OK;
+    DeviceScope ds(h->device);
+    const long long N = h->n;
+    if (pos) CTRY(h, upload(h->staging, pos, sizeof(float) * 3 * N, h->stream), "upload positions");
+    if (vel) CTRY(h, upload(h->staging + 3 * N, vel, sizeof(float) * 3 * N, h->stream), "upload velocities");
+    CTRY(h, launch_aos_to_soa(pos ? h->staging : nullptr, vel ? h->staging + 3 * N : nullptr, h->state,
+                              h->state + 6 * h->stride, h->stride, h->n, h->ctrl, h->stream),
+         "state scatter");
+    return CLOTH_OK;
+}
+
+int cloth_sync(ClothHandle *h)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    DeviceScope ds(h->device);
+    unsigned flags = 0;
+    rc = read_flags(h, &flags);
+    if (rc) return rc;
+    return flags_status(flags);
+}
+
+void cloth_destroy(ClothHandle *h)
+{
+    if (!h) return;
+    {
+        DeviceScope ds(h->device);
+        cudaStreamSynchronize(h->stream);
+        free_all(h);
+        cudaGetLastError();
+    }
+    delete h;
+}
+
+int cloth_get_info(ClothHandle *h, ClothInfo *info)
+{
+    if (!h || !info) return fail(CLOTH_ERR_INVALID_ARG, "null argument");
+    memset(info, 0, sizeof(*info));
+    info->nx = h->desc.nx;
+    info->ny = h->desc.ny;
+    info->n = h->n;
+    info->substeps = h->desc.substeps;
+    info->substeps_done = h->substeps_done;
+    info->plane_stride = h->stride;
+    float *cur = h->state + ((h->substeps_done & 1) ? 6 * h->stride : 0);
+    for (int a = 0; a < 3; a++) {
+        info->pos_planes[a] = cur + a * h->stride;
+        info->vel_planes[a] = cur + (3 + a) * h->stride;
+        info->grid_dims[a] = h->has_mesh ? h->grid.dims[a] : 0;
+        info->grid_origin[a] = h->has_mesh ? h->grid.origin[a] : 0.0f;
+    }
+    info->ntris = h->has_mesh ? h->grid.ntris : 0;
+    info->grid_h = h->has_mesh ? h->grid.h : 0.0f;
+    info->grid_inv = h->has_mesh ? h->grid.inv : 0.0f;
+    info->grid_entries = h->has_mesh ? h->grid.nentries : 0;
+    info->has_per_spring = h->ks_slot != nullptr;
+    return h->dead ? fail(CLOTH_ERR_STATE, "handle unusable after an earlier CUDA error") : CLOTH_OK;
+}
+
+int cloth_get_grid(ClothHandle *h, int32_t *cell_start, int32_t *tri_ids)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!h->has_mesh) return fail(CLOTH_ERR_INVALID_ARG, "no mesh set");
+    DeviceScope ds(h->device);
+    if (cell_start)
+        CTRY(h, cudaMemcpyAsync(cell_start, h->grid.cell_start, sizeof(int) * (size_t)(h->grid.ncells + 1),
+                                cudaMemcpyDeviceToHost, h->stream),
+             "copy cell_start");
+    if (tri_ids && h->grid.nentries > 0)
+        CTRY(h, cudaMemcpyAsync(tri_ids, h->grid.tri_ids, sizeof(int) * (size_t)h->grid.nentries,
+                                cudaMemcpyDeviceToHost, h->stream),
+             "copy tri_ids");
+    CTRY(h, cudaStreamSynchronize(h->stream), "synchronize");
+    return CLOTH_OK;
+}
+
+int cloth_query_candidates(ClothHandle *h, const float *S, const float *E, int32_t nseg, int32_t *counts,
+                           int32_t *ids, int32_t cap)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (nseg < 0 || cap < 0 || (nseg > 0 && (!S || !E || !counts)) || (cap > 0 && !ids))
+        return fail(CLOTH_ERR_INVALID_ARG, "bad query arguments");
+    if (!h->has_mesh) return fail(CLOTH_ERR_INVALID_ARG, "no mesh set");
+    if (nseg == 0) return CLOTH_OK;
+    DeviceScope ds(h->device);
+    float *dS = nullptr, *dE = nullptr;
+    int *dc = nullptr, *di = nullptr;
+    const size_t nb = sizeof(float) * 3 * (size_t)nseg;
+    const size_t ib = sizeof(int) * (size_t)nseg * (size_t)(cap > 0 ? cap : 1);
+    cudaError_t e = cudaMalloc(&dS, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&dE, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&dc, sizeof(int) * (size_t)nseg);
+    if (e == cudaSuccess) e = cudaMalloc(&di, ib);
+    if (e == cudaSuccess) e = upload(dS, S, nb, h->stream);
+    if (e == cudaSuccess) e = upload(dE, E, nb, h->stream);
+    if (e == cudaSuccess) e = grid_query(h->grid, dS, dE, nseg, dc, di, cap, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(counts, dc, sizeof(int) * (size_t)nseg, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && cap > 0) e = cudaMemcpyAsync(ids, di, ib, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dS);
+    cudaFree(dE);
+    cudaFree(dc);
+    cudaFree(di);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(CLOTH_ERR_OOM, "device allocation failed");
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "candidate query");
+    return CLOTH_OK;
+}
+
+}  // extern "C"

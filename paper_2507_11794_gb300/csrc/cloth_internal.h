@@ -1,0 +1,100 @@
+// Internal declarations shared by the translation units of libcloth.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cloth.h"
+
+// Device-side control block of one cloth (one per handle, in device memory).
+struct DevCtrl {
+    unsigned long long k;     // global substep counter: selects time and ping-pong buffer
+    unsigned int blocks_done; // completion counter of the running substep launch
+    unsigned int flags;       // CTRL_FLAG_* (sticky until set_state)
+};
+
+enum : unsigned int { CTRL_FLAG_NONFINITE = 1u, CTRL_FLAG_TIMEOUT = 2u };
+
+// Spring directions (drow, dcol) of the canonical order; each node owns the
+// springs towards these six offsets ("forward"), and receives the other
+// end of the springs of the six nodes at the negated offsets ("backward").
+#define CLOTH_NDIR 6
+
+// Everything one substep launch needs.  Plain data, passed by value.
+struct StepParams {
+    int nx, ny, n;
+    long long stride;          // floats between SoA planes
+    float *state0, *state1;    // 6 planes each: px py pz vx vy vz
+    const uint32_t *pin_bits;  // N bits or nullptr
+    const float *ks_slot;      // 6 planes [dir][node] or nullptr
+    const float *kd_slot;
+    float ks[3], kd[3];        // per type (used without per-spring arrays)
+    float L0[CLOTH_NDIR];      // rest length per direction
+    float inv_mass, dt;
+    float g[3];
+    // wind: phase = omega*t + phase0 + col*kc + row*kr
+    int has_wind;
+    float w_amp, w_dir[3];
+    double w_omega, w_phase0;
+    float w_kc, w_kr;
+    // surface model
+    int has_mesh;
+    const float4 *tri;         // 3 float4 per triangle: (v0, lo.x) (e1, lo.y) (e2, lo.z)
+    const int *cell_start;
+    const int *tri_ids;
+    float go[3];
+    float ginv;
+    int gd[3];
+    float delta, eps, tmin, restitution;
+    DevCtrl *ctrl;
+};
+
+// Launch one substep (reads state k&1, writes the other, advances ctrl->k).
+cudaError_t launch_substep(const StepParams &p, cudaStream_t s);
+
+// Grid over a surface model, built on the device.
+struct DevGrid {
+    float h, inv;
+    float origin[3];
+    int dims[3];
+    long long ncells;
+    long long nentries;
+    float4 *tri;       // 3 per triangle
+    int *cell_start;   // ncells + 1
+    int *tri_ids;      // nentries
+    int ntris;
+};
+
+// Host-side grid parameters (FP64 mean of the triangles' longest AABB side).
+int grid_params(const float *verts, const int32_t *tris, int32_t nt, float *h, float origin[3], int dims[3],
+                float *inv);
+
+// Build the device grid from device copies of the mesh (d_verts, d_tris).
+// Allocates g->tri, g->cell_start, g->tri_ids; scratch is allocated and
+// freed inside.  Synchronises s.
+cudaError_t grid_build(const float *d_verts, const int *d_tris, int ntris, DevGrid *g, cudaStream_t s);
+void grid_free(DevGrid *g);
+
+// Candidate query for debug/tests: counts[i], ids[i*cap..] (device arrays).
+cudaError_t grid_query(const DevGrid &g, const float *dS, const float *dE, int nseg, int *counts, int *ids, int cap,
+                       cudaStream_t s);
+
+// AoS <-> SoA state transfer through the ping-pong buffer selected by ctrl->k.
+cudaError_t launch_aos_to_soa(const float *aos_pos, const float *aos_vel, float *state0, float *state1,
+                              long long stride, int n, DevCtrl *ctrl, cudaStream_t s);
+cudaError_t launch_soa_to_aos(const float *state0, const float *state1, long long stride, int n,
+                              const DevCtrl *ctrl, float *aos_pos, float *aos_vel, cudaStream_t s);
+
+#ifdef __CUDACC__
+// Grid cell coordinate of one float coordinate: floor((x - o) * inv) in
+// float32, round-to-nearest with no contraction, clamped to [0, dim-1]
+// (NaN -> 0).  Broad-phase candidate sets are defined by this formula, so it
+// must stay exactly this sequence of rounded operations.
+__device__ __forceinline__ int cell_coord(float x, float o, float inv, int dim)
+{
+    float f = floorf(__fmul_rn(__fsub_rn(x, o), inv));
+    if (!(f >= 0.0f)) f = 0.0f;
+    if (f > (float)(dim - 1)) f = (float)(dim - 1);
+    return (int)f;
+}
+#endif

@@ -1,0 +1,122 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports
+every symbol include/cloth.h declares, the ctypes mirror of every struct has
+the C layout, and argument validation answers without touching a GPU."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cloth.h")
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2507_11794_gb300 import build as B
+    B.build()
+    from paper_2507_11794_gb300 import capi as A
+    A.lib()
+    return A
+
+
+def header_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cloth_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for required in ("cloth_create", "cloth_set_mesh", "cloth_step", "cloth_read", "cloth_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(capi):
+    out = subprocess.run(["nm", "-D", "--defined-only", capi.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (cloth_\w+)", out))
+    declared = set(header_functions())
+    assert declared <= exported, declared - exported
+    assert set(capi.EXPORTS) == declared
+
+
+def test_struct_layout_matches_c(capi, tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(r'''
+#include <stddef.h>
+#include <stdio.h>
+#include "cloth.h"
+#define F(T, m) printf(#T "." #m " %zu\n", offsetof(T, m))
+int main(void) {
+  printf("ClothDesc %zu\nClothWind %zu\nClothInfo %zu\n", sizeof(ClothDesc), sizeof(ClothWind), sizeof(ClothInfo));
+  F(ClothDesc, ks_spring); F(ClothDesc, pinned); F(ClothDesc, gravity); F(ClothDesc, dt);
+  F(ClothDesc, substeps); F(ClothDesc, mt_t_min); F(ClothDesc, wind); F(ClothDesc, flags);
+  F(ClothInfo, substeps_done); F(ClothInfo, pos_planes); F(ClothInfo, vel_planes); F(ClothInfo, ntris);
+  F(ClothInfo, grid_h); F(ClothInfo, grid_entries); F(ClothInfo, has_per_spring);
+  return 0;
+}''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(l.rsplit(" ", 1) for l in lines if l)
+    assert int(got["ClothDesc"]) == C.sizeof(capi.ClothDesc)
+    assert int(got["ClothWind"]) == C.sizeof(capi.ClothWind)
+    assert int(got["ClothInfo"]) == C.sizeof(capi.ClothInfo)
+    for key, val in got.items():
+        if "." in key:
+            T, m = key.split(".")
+            assert int(val) == getattr(getattr(capi, T), m).offset, key
+
+
+def _desc(capi, **kw):
+    d = capi.ClothDesc()
+    d.nx, d.ny = kw.get("nx", 4), kw.get("ny", 4)
+    d.du[0], d.dv[2] = 0.1, 0.1
+    d.total_mass = kw.get("total_mass", 1.0)
+    d.dt = kw.get("dt", 1e-3)
+    d.substeps = kw.get("substeps", 1)
+    d.mt_eps = 1e-7
+    d.restitution = -0.5
+    return d
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("ny", -3), ("substeps", 0), ("dt", 0.0), ("dt", float("nan")),
+                                         ("total_mass", 0.0)])
+def test_create_rejects_bad_desc_without_gpu(capi, field, value):
+    # validation happens on the host before any CUDA call
+    d = _desc(capi, **{field: value})
+    h = C.c_void_p()
+    rc = capi.lib().cloth_create(C.byref(d), None, C.byref(h))
+    assert rc == capi.CLOTH_ERR_INVALID_ARG
+    assert h.value is None
+    assert capi.lib().cloth_last_error()
+
+
+def test_null_arguments_are_rejected(capi):
+    L = capi.lib()
+    h = C.c_void_p()
+    assert L.cloth_create(None, None, C.byref(h)) == capi.CLOTH_ERR_INVALID_ARG
+    assert L.cloth_create(C.byref(_desc(capi)), None, None) == capi.CLOTH_ERR_INVALID_ARG
+    assert L.cloth_step(None, 1) == capi.CLOTH_ERR_INVALID_ARG
+    assert L.cloth_read(None, None, None) == capi.CLOTH_ERR_INVALID_ARG
+    assert L.cloth_set_mesh(None, None, 0, None, 0) == capi.CLOTH_ERR_INVALID_ARG
+    assert L.cloth_sync(None) == capi.CLOTH_ERR_INVALID_ARG
+    L.cloth_destroy(None)  # NULL-safe
+
+
+def test_nonfinite_parameters_are_rejected(capi):
+    d = _desc(capi)
+    d.gravity[1] = float("inf")
+    h = C.c_void_p()
+    assert capi.lib().cloth_create(C.byref(d), None, C.byref(h)) == capi.CLOTH_ERR_INVALID_ARG
+    assert b"non-finite" in capi.lib().cloth_last_error()
+
+
+def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2507_11794_gb300 import capi as A
+    monkeypatch.setattr(A, "_lib", None)
+    monkeypatch.setattr(A, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        A.lib()
