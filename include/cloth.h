@@ -179,6 +179,59 @@ int cloth_get_grid(ClothHandle *h, int32_t *cell_start, int32_t *tri_ids);
 int cloth_query_candidates(ClothHandle *h, const float *S, const float *E, int32_t nseg,
                            int32_t *counts, int32_t *ids, int32_t cap);
 
+/* ---- allocation-free grid build --------------------------------------- */
+
+/* Largest mesh and grid cloth_grid_build_static accepts. */
+#define CLOTH_STATIC_GRID_MAX_TRIS 131072
+#define CLOTH_STATIC_GRID_MAX_VERTS 131072
+#define CLOTH_STATIC_GRID_MAX_CELLS 262144
+
+typedef struct ClothGridParams {
+    float h, inv;       /* cell size and its float reciprocal */
+    float origin[3];    /* corner of cell (0,0,0) */
+    int32_t dims[3];    /* cells per axis; cell id = (z*dims[1] + y)*dims[0] + x */
+    int64_t ncells;     /* dims[0]*dims[1]*dims[2] */
+    int64_t nentries;   /* (cell, triangle) pairs = length of tri_ids; -1 if not counted */
+} ClothGridParams;
+
+/* The paper has no counterpart to this entry point: it is a variant of the
+ * grid build inside cloth_set_mesh for callers that must not allocate device
+ * memory -- code that runs while a CUDA graph is being captured, inside
+ * another library's stream-ordered region, or under an allocator with a fixed
+ * budget or a ban on cudaMalloc/cudaFree after start-up.  It allocates
+ * nothing: its temporaries live in one fixed-size device array of the library
+ * (7,341,312 bytes, held on every GPU that loads the library until the
+ * process exits), and the caller supplies the outputs.
+ *
+ * Inputs: host arrays verts [nverts][3] float32 and tris [ntris][3] int32
+ * (the same mesh cloth_set_mesh takes), at most CLOTH_STATIC_GRID_MAX_TRIS
+ * triangles, CLOTH_STATIC_GRID_MAX_VERTS vertices and a grid of at most
+ * CLOTH_STATIC_GRID_MAX_CELLS cells; larger inputs are rejected with
+ * CLOTH_ERR_INVALID_ARG before any GPU work.  stream: the cudaStream_t to run
+ * on (NULL = legacy default stream); the call synchronises it.
+ * Outputs (caller-owned device memory of the current device):
+ *   d_tri_records  12*ntris floats, 16-byte aligned: per triangle the float4s
+ *                  (v0, lo.x) (v1-v0, lo.y) (v2-v0, lo.z), lo = first cell;
+ *   d_cell_start   cell_capacity >= ncells+1 ints (exclusive prefix of counts);
+ *   d_tri_ids      entry_capacity >= nentries ints, each cell's ids ascending.
+ * params receives the grid parameters, nentries once counted.  If a capacity
+ * is too small the call returns CLOTH_ERR_INVALID_ARG with params filled as
+ * far as known (ncells always, nentries when the cells fitted), so a caller
+ * can size its buffers with calls of zero capacity.  The results are
+ * identical to the grid cloth_set_mesh builds for the same mesh.
+ *
+ * Every call shares the one scratch array and leaves its last contents
+ * there; each call clears what must start at zero.  Calls whose GPU work
+ * overlaps (on different streams, or from different threads on the same
+ * device) race on the scratch and give wrong results: serialise them.  The
+ * first call on each device looks the array's device address up (with that
+ * device current) and should come before any stream capture on that device.
+ * Errors: CLOTH_ERR_INVALID_ARG, CLOTH_ERR_BAD_MESH (index out of range,
+ * non-finite vertex), CLOTH_ERR_CUDA. */
+int cloth_grid_build_static(const float *verts, int32_t nverts, const int32_t *tris, int32_t ntris, void *stream,
+                            float *d_tri_records, int32_t *d_cell_start, int64_t cell_capacity,
+                            int32_t *d_tri_ids, int64_t entry_capacity, ClothGridParams *params);
+
 #ifdef __cplusplus
 }
 #endif

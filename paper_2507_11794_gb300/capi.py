@@ -33,7 +33,7 @@ _NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5
 # Every symbol include/cloth.h declares (checked by the CPU test-suite).
 EXPORTS = ("cloth_create", "cloth_set_mesh", "cloth_step", "cloth_read", "cloth_destroy",
            "cloth_set_state", "cloth_sync", "cloth_last_error", "cloth_get_info", "cloth_get_grid",
-           "cloth_query_candidates")
+           "cloth_query_candidates", "cloth_grid_build_static")
 
 
 class ClothError(RuntimeError):
@@ -76,6 +76,11 @@ class ClothInfo(C.Structure):
     ]
 
 
+class ClothGridParams(C.Structure):
+    _fields_ = [("h", C.c_float), ("inv", C.c_float), ("origin", C.c_float * 3), ("dims", C.c_int32 * 3),
+                ("ncells", C.c_int64), ("nentries", C.c_int64)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -105,6 +110,8 @@ def lib():
         L.cloth_get_info.argtypes = [H, C.POINTER(ClothInfo)]
         L.cloth_get_grid.argtypes = [H, ip, ip]
         L.cloth_query_candidates.argtypes = [H, fp, fp, C.c_int32, ip, ip, C.c_int32]
+        L.cloth_grid_build_static.argtypes = [fp, C.c_int32, ip, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_int64, C.c_void_p, C.c_int64, C.POINTER(ClothGridParams)]
         for name in EXPORTS:
             f = getattr(L, name)
             if name not in ("cloth_destroy", "cloth_last_error"):
@@ -201,3 +208,17 @@ def cloth_query_candidates(h: int, S, E, cap: int = 64):
         if n == 0 or counts.max() <= cap:
             return counts, ids
         cap = int(counts.max())
+
+
+def cloth_grid_build_static(verts, tris, stream, d_tri_records, d_cell_start, cell_capacity, d_tri_ids,
+                            entry_capacity):
+    """Allocation-free grid build into caller device buffers (raw device
+    addresses as ints).  Returns (status, ClothGridParams); does not raise, so
+    callers can size buffers from a CLOTH_ERR_INVALID_ARG answer."""
+    v = f32(verts, (-1, 3))
+    t = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+    prm = ClothGridParams()
+    rc = lib().cloth_grid_build_static(_fp(v), len(v), _ip(t), len(t), C.c_void_p(stream),
+                                       C.c_void_p(d_tri_records), C.c_void_p(d_cell_start), int(cell_capacity),
+                                       C.c_void_p(d_tri_ids), int(entry_capacity), C.byref(prm))
+    return rc, prm

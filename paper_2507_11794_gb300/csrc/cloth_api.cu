@@ -220,6 +220,9 @@ cudaError_t upload(void *dst, const void *src, size_t bytes, cudaStream_t s)
 
 }  // namespace
 
+// Lets other translation units report through cloth_last_error().
+void cloth_set_error_message(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 extern "C" {
 
 const char *cloth_last_error(void) { return g_err; }

@@ -352,3 +352,40 @@ cudaError_t grid_query(const DevGrid &g, const float *dS, const float *dE, int n
                                                        nseg, counts, ids, cap);
     return cudaGetLastError();
 }
+
+// Grid build with every temporary buffer supplied by the caller (no
+// allocation).  Same kernels and order as grid_build.  Writes the pair count
+// to *nentries after the counting pass; when it exceeds entry_cap nothing
+// more is written and *done is false.  Synchronises s.
+cudaError_t grid_build_noalloc(const float *d_verts, const int *d_tris, int nt, const float origin[3], float inv,
+                               const int dims[3], float4 *rec, int *cell_start, int *tri_ids, long long entry_cap,
+                               int4 *box_hi, unsigned *cnt, unsigned *cursor, unsigned *sums,
+                               unsigned long long *total, long long *nentries, bool *done, cudaStream_t s)
+{
+    const long long nc = (long long)dims[0] * dims[1] * dims[2];
+    const long long ntiles = (nc + SCAN_TILE - 1) / SCAN_TILE;
+    unsigned long long htotal = 0;
+    cudaError_t e;
+    *done = false;
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (size_t)nc, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(cursor, 0, sizeof(unsigned) * (size_t)nc, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(total, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    tri_prep_kernel<<<blocks_for(nt, 256), 256, 0, s>>>(d_verts, d_tris, nt, origin[0], origin[1], origin[2], inv,
+                                                        dims[0], dims[1], dims[2], rec, box_hi, total);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(&htotal, total, sizeof(htotal), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    *nentries = (long long)htotal;
+    if ((long long)htotal > entry_cap) return cudaSuccess;
+    cell_count_kernel<<<blocks_for(nt, 256), 256, 0, s>>>(rec, box_hi, nt, dims[0], dims[1], cnt);
+    scan_reduce_kernel<<<(int)ntiles, SCAN_THREADS, 0, s>>>(cnt, nc, sums);
+    scan_sums_kernel<<<1, SCAN_THREADS, 0, s>>>(sums, ntiles);
+    scan_final_kernel<<<(int)ntiles, SCAN_THREADS, 0, s>>>(cnt, nc, sums, cell_start);
+    cell_fill_kernel<<<blocks_for(nt, 256), 256, 0, s>>>(rec, box_hi, nt, dims[0], dims[1], cell_start, cursor,
+                                                         tri_ids);
+    cell_sort_kernel<<<blocks_for(nc, 256), 256, 0, s>>>(cell_start, nc, tri_ids);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    *done = true;
+    return cudaSuccess;
+}

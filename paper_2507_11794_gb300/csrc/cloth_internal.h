@@ -98,3 +98,13 @@ __device__ __forceinline__ int cell_coord(float x, float o, float inv, int dim)
     return (int)f;
 }
 #endif
+
+// Grid build into caller-supplied outputs and scratch (no allocation); see
+// cloth_grid.cu.
+cudaError_t grid_build_noalloc(const float *d_verts, const int *d_tris, int nt, const float origin[3], float inv,
+                               const int dims[3], float4 *rec, int *cell_start, int *tri_ids, long long entry_cap,
+                               int4 *box_hi, unsigned *cnt, unsigned *cursor, unsigned *sums,
+                               unsigned long long *total, long long *nentries, bool *done, cudaStream_t s);
+
+// Sets the calling thread's cloth_last_error() message.
+void cloth_set_error_message(const char *msg);
