@@ -154,14 +154,16 @@ typedef struct ClothInfo {
     int32_t substeps;
     int64_t substeps_done;     /* substeps enqueued since create */
     int64_t plane_stride;      /* floats between consecutive SoA planes */
-    float *pos_planes[3];      /* device pointers of the current x,y,z planes */
-    float *vel_planes[3];      /* (valid until the next cloth_step/set_state) */
+    float *pos_planes[3];      /* device pointers of the current x,y,z planes: node */
+    float *vel_planes[3];      /* (row,col) at [row*row_pitch + col]; valid once the
+                                  enqueued work has run, until the next step/set_state */
     int32_t ntris;
     int32_t grid_dims[3];
     float grid_origin[3];
     float grid_h, grid_inv;
     int64_t grid_entries;
     int32_t has_per_spring;
+    int32_t row_pitch;         /* floats per row in the SoA planes (nx rounded up to 4) */
 } ClothInfo;
 
 /* Sizes, grid parameters and device pointers of the current SoA state. */

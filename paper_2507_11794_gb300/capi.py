@@ -72,7 +72,7 @@ class ClothInfo(C.Structure):
         ("pos_planes", C.c_void_p * 3), ("vel_planes", C.c_void_p * 3),
         ("ntris", C.c_int32), ("grid_dims", C.c_int32 * 3), ("grid_origin", C.c_float * 3),
         ("grid_h", C.c_float), ("grid_inv", C.c_float), ("grid_entries", C.c_int64),
-        ("has_per_spring", C.c_int32),
+        ("has_per_spring", C.c_int32), ("row_pitch", C.c_int32),
     ]
 
 

@@ -14,6 +14,8 @@
 struct ClothHandle {
     ClothDesc desc;  // array pointers cleared after the copy
     int n = 0;
+    int pitch = 0;           // floats per row: nx rounded up to 4
+    int sm_count = 0;
     long long stride = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -23,6 +25,7 @@ struct ClothHandle {
     float *ks_slot = nullptr, *kd_slot = nullptr;
     DevCtrl *ctrl = nullptr;
     float *staging = nullptr;  // 6*n floats for AoS transfers
+    int *coll_list = nullptr;  // n entries
     DevGrid grid{};
     bool has_mesh = false;
     StepParams params{};
@@ -95,6 +98,8 @@ void free_all(ClothHandle *h)
     cudaFree(h->kd_slot);
     cudaFree(h->ctrl);
     cudaFree(h->staging);
+    cudaFree(h->coll_list);
+    h->coll_list = nullptr;
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->state = nullptr;
     h->pin_bits = nullptr;
@@ -111,6 +116,9 @@ void fill_params(ClothHandle *h)
     p.nx = d.nx;
     p.ny = d.ny;
     p.n = h->n;
+    p.pitch = h->pitch;
+    p.rows_per_warp = substep_rows_per_warp(d.nx, d.ny, h->sm_count);
+    substep_shape(p);
     p.stride = h->stride;
     p.state0 = h->state;
     p.state1 = h->state + 6 * h->stride;
@@ -157,11 +165,21 @@ void fill_params(ClothHandle *h)
         p.gd[a] = h->grid.dims[a];
     }
     p.ginv = h->grid.inv;
+    for (int a = 0; a < 3; a++) {
+        // box of the non-border cells 1..dims-2 (border cells hold no triangle),
+        // widened by 1% of a cell against rounding of the cell formula
+        p.mlo[a] = h->has_mesh ? (float)((double)h->grid.origin[a] + 0.99 * (double)h->grid.h) : 0.0f;
+        p.mhi[a] = h->has_mesh ? (float)((double)h->grid.origin[a] + ((double)h->grid.dims[a] - 0.99) * h->grid.h)
+                               : 0.0f;
+    }
     p.delta = d.contact_offset;
     p.eps = d.mt_eps;
     p.tmin = d.mt_t_min;
     p.restitution = d.restitution;
     p.ctrl = h->ctrl;
+    p.coll_list = h->coll_list;
+    p.coll_count = h->ctrl ? &h->ctrl->coll_count : nullptr;
+    p.coll_blocks = h->sm_count * 8;
 }
 
 void invalidate_graph(ClothHandle *h)
@@ -266,9 +284,14 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
     h->desc.init_pos = h->desc.init_vel = nullptr;
     h->desc.pinned = nullptr;
     h->n = (int)N;
-    h->stride = (N + 63) / 64 * 64;  // 256-byte aligned planes
+    h->pitch = (d.nx + 3) / 4 * 4;                                          // 16-byte aligned rows
+    h->stride = ((long long)h->pitch * d.ny + 63) / 64 * 64;                // 256-byte aligned planes
     h->stream = (cudaStream_t)stream;
     cudaGetDevice(&h->device);
+    if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+        h->sm_count < 1)
+        h->sm_count = 152;
+    cudaGetLastError();
 
     int rc = CLOTH_OK;
     cudaError_t e = cudaSuccess;
@@ -278,6 +301,7 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
         if ((e = cudaMalloc(&h->state, sizeof(float) * 12 * (size_t)h->stride)) != cudaSuccess) break;
         if ((e = cudaMalloc(&h->ctrl, sizeof(DevCtrl))) != cudaSuccess) break;
         if ((e = cudaMalloc(&h->staging, sizeof(float) * 6 * (size_t)N)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&h->coll_list, sizeof(int) * (size_t)N)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(h->ctrl, 0, sizeof(DevCtrl), h->stream)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(h->state, 0, sizeof(float) * 12 * (size_t)h->stride, h->stream)) != cudaSuccess)
             break;
@@ -293,14 +317,17 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
         }
         if ((e = upload(h->staging, init.data(), sizeof(float) * 6 * (size_t)N, h->stream)) != cudaSuccess) break;
         if ((e = launch_aos_to_soa(h->staging, h->staging + 3 * N, h->state, h->state + 6 * h->stride, h->stride,
-                                   (int)N, h->ctrl, h->stream)) != cudaSuccess)
+                                   (int)N, d.nx, h->pitch, h->ctrl, h->stream)) != cudaSuccess)
             break;
         if (d.pinned) {
-            std::vector<uint32_t> bits((size_t)(N + 31) / 32, 0u);
+            // one bit per padded position r*pitch + c
+            const long long nb = (long long)h->pitch * d.ny;
+            std::vector<uint32_t> bits((size_t)(nb + 31) / 32, 0u);
             bool any = false;
             for (long long i = 0; i < N; i++)
                 if (d.pinned[i]) {
-                    bits[(size_t)(i >> 5)] |= 1u << (i & 31);
+                    const long long b = (i / d.nx) * h->pitch + (i % d.nx);
+                    bits[(size_t)(b >> 5)] |= 1u << (b & 31);
                     any = true;
                 }
             if (any) {
@@ -319,7 +346,7 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
                     for (int k = 0; k < CLOTH_NDIR; k++) {
                         const long long r2 = r + kDR[k], c2 = c + kDC[k];
                         if (r2 < 0 || r2 >= d.ny || c2 < 0 || c2 >= d.nx) continue;
-                        const size_t slot = (size_t)k * h->stride + (size_t)(r * d.nx + c);
+                        const size_t slot = (size_t)k * h->stride + (size_t)(r * h->pitch + c);
                         ks[slot] = d.ks_spring ? d.ks_spring[s] : d.ks[type[k]];
                         kd[slot] = d.kd_spring ? d.kd_spring[s] : d.kd[type[k]];
                         s++;
@@ -420,7 +447,7 @@ int cloth_read(ClothHandle *h, float *pos_out, float *vel_out)
     const long long N = h->n;
     unsigned flags = 0;
     if (pos_out || vel_out) {
-        CTRY(h, launch_soa_to_aos(h->state, h->state + 6 * h->stride, h->stride, h->n, h->ctrl,
+        CTRY(h, launch_soa_to_aos(h->state, h->state + 6 * h->stride, h->stride, h->n, h->desc.nx, h->pitch, h->ctrl,
                                   pos_out ? h->staging : nullptr, vel_out ? h->staging + 3 * N : nullptr, h->stream),
              "state gather");
         if (pos_out)
@@ -446,7 +473,7 @@ int cloth_set_state(ClothHandle *h, const float *pos, const float *vel)
     if (pos) CTRY(h, upload(h->staging, pos, sizeof(float) * 3 * N, h->stream), "upload positions");
     if (vel) CTRY(h, upload(h->staging + 3 * N, vel, sizeof(float) * 3 * N, h->stream), "upload velocities");
     CTRY(h, launch_aos_to_soa(pos ? h->staging : nullptr, vel ? h->staging + 3 * N : nullptr, h->state,
-                              h->state + 6 * h->stride, h->stride, h->n, h->ctrl, h->stream),
+                              h->state + 6 * h->stride, h->stride, h->n, h->desc.nx, h->pitch, h->ctrl, h->stream),
          "state scatter");
     return CLOTH_OK;
 }
@@ -496,6 +523,7 @@ int cloth_get_info(ClothHandle *h, ClothInfo *info)
     info->grid_inv = h->has_mesh ? h->grid.inv : 0.0f;
     info->grid_entries = h->has_mesh ? h->grid.nentries : 0;
     info->has_per_spring = h->ks_slot != nullptr;
+    info->row_pitch = h->pitch;
     return h->dead ? fail(CLOTH_ERR_STATE, "handle unusable after an earlier CUDA error") : CLOTH_OK;
 }
 

@@ -11,6 +11,8 @@ struct DevCtrl {
     unsigned long long k;     // global substep counter: selects time and ping-pong buffer
     unsigned int blocks_done; // completion counter of the running substep launch
     unsigned int flags;       // CTRL_FLAG_* (sticky until set_state)
+    unsigned int coll_count;  // marked nodes of the running substep
+    unsigned int pad;
 };
 
 enum : unsigned int { CTRL_FLAG_NONFINITE = 1u, CTRL_FLAG_TIMEOUT = 2u };
@@ -23,10 +25,13 @@ enum : unsigned int { CTRL_FLAG_NONFINITE = 1u, CTRL_FLAG_TIMEOUT = 2u };
 // Everything one substep launch needs.  Plain data, passed by value.
 struct StepParams {
     int nx, ny, n;
+    int pitch;                 // floats per row (nx rounded up to 4): node (r,c) at r*pitch + c
+    int rows_per_warp;         // rows walked by one warp
+    int strips_x, strips_y;    // warp strips across columns / rows
     long long stride;          // floats between SoA planes
     float *state0, *state1;    // 6 planes each: px py pz vx vy vz
-    const uint32_t *pin_bits;  // N bits or nullptr
-    const float *ks_slot;      // 6 planes [dir][node] or nullptr
+    const uint32_t *pin_bits;  // one bit per r*pitch + c, or nullptr
+    const float *ks_slot;      // 6 planes [dir][r*pitch + c] (0 where no spring) or nullptr
     const float *kd_slot;
     float ks[3], kd[3];        // per type (used without per-spring arrays)
     float L0[CLOTH_NDIR];      // rest length per direction
@@ -45,12 +50,19 @@ struct StepParams {
     float go[3];
     float ginv;
     int gd[3];
+    float mlo[3], mhi[3];      // box of the grid's non-border cells (early out)
+    int *coll_list;            // node offsets marked for the collision kernel (capacity N)
+    unsigned *coll_count;      // entries in coll_list (reset by the collision kernel)
+    int coll_blocks;           // CTAs of the collision kernel
     float delta, eps, tmin, restitution;
     DevCtrl *ctrl;
 };
 
 // Launch one substep (reads state k&1, writes the other, advances ctrl->k).
 cudaError_t launch_substep(const StepParams &p, cudaStream_t s);
+// Rows per warp of the column walk for a grid and SM count; strips from it.
+int substep_rows_per_warp(int nx, int ny, int sm_count);
+void substep_shape(StepParams &p);
 
 // Grid over a surface model, built on the device.
 struct DevGrid {
@@ -81,8 +93,8 @@ cudaError_t grid_query(const DevGrid &g, const float *dS, const float *dE, int n
 
 // AoS <-> SoA state transfer through the ping-pong buffer selected by ctrl->k.
 cudaError_t launch_aos_to_soa(const float *aos_pos, const float *aos_vel, float *state0, float *state1,
-                              long long stride, int n, DevCtrl *ctrl, cudaStream_t s);
-cudaError_t launch_soa_to_aos(const float *state0, const float *state1, long long stride, int n,
+                              long long stride, int n, int nx, int pitch, DevCtrl *ctrl, cudaStream_t s);
+cudaError_t launch_soa_to_aos(const float *state0, const float *state1, long long stride, int n, int nx, int pitch,
                               const DevCtrl *ctrl, float *aos_pos, float *aos_vel, cudaStream_t s);
 
 #ifdef __CUDACC__

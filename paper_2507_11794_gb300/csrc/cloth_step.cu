@@ -1,68 +1,182 @@
 // One substep of the mass-spring cloth, fused into a single kernel:
-//   spring + damping forces (Algorithm 1's force law, gathered per node),
-//   symplectic Euler with gravity, wind and pins (Section 3),
+//   spring + damping forces (Algorithm 1's force law, each spring evaluated
+//   once), symplectic Euler with gravity, wind and pins (Section 3),
 //   uniform-grid broad phase + extended Moller-Trumbore narrow phase on the
 //   node's substep path (Section 3) and the averaged response of Algorithm 2.
 //
-// Layout: six SoA float planes (px py pz vx vy vz) per ping-pong buffer; the
-// launch reads buffer k&1 and writes the other, k = the device substep counter.
-// Each CTA stages a TX x TY node tile plus a two-node halo (bend springs reach
-// two nodes) of all six planes in shared memory, then each thread gathers the
-// twelve springs of its nodes from shared memory: no atomics, fixed summation
-// order, so results are bitwise reproducible run to run.
+// Layout: six SoA float planes (px py pz vx vy vz) per ping-pong buffer, rows
+// of `pitch` floats (nx rounded up to 4); the launch reads buffer k&1 and
+// writes the other, k = the device substep counter.
+//
+// Work decomposition (register-window column walk): each lane owns two
+// adjacent columns (A = even, B = odd) held as float2 pairs, so every
+// arithmetic instruction of the spring law works on both nodes at once
+// (packed FP32x2).  A warp covers 64 columns, of which lanes 1..30 produce
+// output (60 columns) and lanes 0 and 31 are the halo that bend springs need.
+// The warp walks down `rows_per_warp` rows keeping rows r, r+1, r+2 in
+// registers; neighbour data moves between lanes by shuffles.  Each node
+// evaluates only its six "forward" springs (towards (0,+1), (0,+2), (+1,0),
+// (+2,0), (+1,+1), (+1,-1)); the reaction -F of Algorithm 1 reaches the other
+// end by shuffle (same row) or is carried in registers to the next rows.  So
+// every spring is evaluated once, with no atomics and a fixed summation order:
+// results are bitwise reproducible.  The first two rows of each walk only
+// produce the springs that reach into the strip.
 #include "cloth_internal.h"
 
 namespace {
 
-constexpr int TX = 32;           // tile columns (one warp)
-constexpr int TY = 16;           // tile rows
-constexpr int BY = 8;            // thread rows per CTA; each thread owns TY/BY nodes
-constexpr int HALO = 2;
-constexpr int SX = TX + 2 * HALO;
-constexpr int SY = TY + 2 * HALO;
-constexpr int NTHREADS = TX * BY;
+// Tuning knobs of the walk kernel (defaults chosen by measurement):
+// CTAs per SM the register budget targets, and the unroll of the row walk.
+#ifndef CLOTH_WALK_MINB
+#define CLOTH_WALK_MINB 2
+#endif
+#ifndef CLOTH_WALK_UNROLL
+#define CLOTH_WALK_UNROLL 1
+#endif
+#define CLOTH_PRAGMA(x) _Pragma(#x)
+#define CLOTH_UNROLL(n) CLOTH_PRAGMA(unroll n)
 
-__device__ __forceinline__ void spring_add(float pix, float piy, float piz, float vix, float viy, float viz,
-                                           float pjx, float pjy, float pjz, float vjx, float vjy, float vjz,
-                                           float ks, float kd, float L0, float &fx, float &fy, float &fz)
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int WARPS_PER_CTA = 4;
+constexpr int STRIP_COLS = 60;
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b, exact as one rounding: fma(b, -1, a)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
+
+struct Node2 {  // two nodes (A = .x, B = .y)
+    float2 px, py, pz, vx, vy, vz;
+};
+struct Vec2 {  // one 3-vector per node of the pair
+    float2 x, y, z;
+};
+
+__device__ __forceinline__ Vec2 vadd(Vec2 a, Vec2 b) { return {add2(a.x, b.x), add2(a.y, b.y), add2(a.z, b.z)}; }
+__device__ __forceinline__ Vec2 vsub(Vec2 a, Vec2 b) { return {sub2(a.x, b.x), sub2(a.y, b.y), sub2(a.z, b.z)}; }
+
+__device__ __forceinline__ float2 shfl_down2(float2 v, int d)
 {
-    // Hooke's law plus damping along the spring (Algorithm 1), seen from node i:
-    // d = p_j - p_i, F_i += (ks (|d| - L0) + kd (v_j - v_i).d^) d^.
-    float dx = pjx - pix, dy = pjy - piy, dz = pjz - piz;
-    float l2 = dx * dx + dy * dy + dz * dz;
-    if (l2 > 1e-24f) {
-        float il = rsqrtf(l2);
-        float l = l2 * il;
-        float ux = dx * il, uy = dy * il, uz = dz * il;
-        float dvn = (vjx - vix) * ux + (vjy - viy) * uy + (vjz - viz) * uz;
-        float f = ks * (l - L0) + kd * dvn;
-        fx += f * ux;
-        fy += f * uy;
-        fz += f * uz;
+    return make_float2(__shfl_down_sync(FULL, v.x, d), __shfl_down_sync(FULL, v.y, d));
+}
+__device__ __forceinline__ float2 shfl_up2(float2 v, int d)
+{
+    return make_float2(__shfl_up_sync(FULL, v.x, d), __shfl_up_sync(FULL, v.y, d));
+}
+__device__ __forceinline__ Node2 shfl_down_node(const Node2 &n)
+{
+    return {shfl_down2(n.px, 1), shfl_down2(n.py, 1), shfl_down2(n.pz, 1),
+            shfl_down2(n.vx, 1), shfl_down2(n.vy, 1), shfl_down2(n.vz, 1)};
+}
+
+// Row r of the lane's two columns (zeros outside the grid's rows / memory).
+__device__ __forceinline__ Node2 load_row(const float *__restrict__ in, long long st, int pitch, int r, int ny, int cA,
+                                          bool colmem)
+{
+    Node2 n;
+    if (r >= 0 && r < ny && colmem) {
+        const float *b = in + (long long)r * pitch + cA;
+        n.px = __ldg((const float2 *)(b));
+        n.py = __ldg((const float2 *)(b + st));
+        n.pz = __ldg((const float2 *)(b + 2 * st));
+        n.vx = __ldg((const float2 *)(b + 3 * st));
+        n.vy = __ldg((const float2 *)(b + 4 * st));
+        n.vz = __ldg((const float2 *)(b + 5 * st));
+    } else {
+        n.px = n.py = n.pz = n.vx = n.vy = n.vz = make_float2(0.0f, 0.0f);
     }
+    return n;
+}
+
+// Hooke's law plus damping along the spring (Algorithm 1) for the pair:
+// d = q - p, F_p = (ks (|d| - L0) + kd (v_q - v_p).d^) d^ (zero for |d|^2 <= 1e-24).
+__device__ __forceinline__ Vec2 spring2(const Node2 &P, const Node2 &Q, float2 ks, float2 kd, float L0)
+{
+    const float2 dx = sub2(Q.px, P.px), dy = sub2(Q.py, P.py), dz = sub2(Q.pz, P.pz);
+    const float2 l2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    float2 il;
+    il.x = l2.x > 1e-24f ? rsqrtf(l2.x) : 0.0f;
+    il.y = l2.y > 1e-24f ? rsqrtf(l2.y) : 0.0f;
+    const float2 l = mul2(l2, il);
+    const float2 ux = mul2(dx, il), uy = mul2(dy, il), uz = mul2(dz, il);
+    const float2 dvn = fma2(sub2(Q.vz, P.vz), uz, fma2(sub2(Q.vy, P.vy), uy, mul2(sub2(Q.vx, P.vx), ux)));
+    const float2 s = fma2(kd, dvn, mul2(ks, add2(l, bc(-L0))));
+    return {mul2(s, ux), mul2(s, uy), mul2(s, uz)};
+}
+
+// Broad + narrow phase and response of one node (scalar).  S = start, E =
+// predicted end; on K > 0 hits returns true and the response position.
+__device__ __forceinline__ bool collide(const StepParams &p, float sx, float sy, float sz, float ex, float ey, float ez,
+                                     float &ox, float &oy, float &oz)
+{
+    const float dx = ex - sx, dy = ey - sy, dz = ez - sz;
+    const float L = sqrtf(dx * dx + dy * dy + dz * dz);
+    if (!(L >= p.eps)) return false;
+    const float rx = dx / L, ry = dy / L, rz = dz / L;
+    const int lox = cell_coord(fminf(sx, ex), p.go[0], p.ginv, p.gd[0]);
+    const int hix = cell_coord(fmaxf(sx, ex), p.go[0], p.ginv, p.gd[0]);
+    const int loy = cell_coord(fminf(sy, ey), p.go[1], p.ginv, p.gd[1]);
+    const int hiy = cell_coord(fmaxf(sy, ey), p.go[1], p.ginv, p.gd[1]);
+    const int loz = cell_coord(fminf(sz, ez), p.go[2], p.ginv, p.gd[2]);
+    const int hiz = cell_coord(fmaxf(sz, ez), p.go[2], p.ginv, p.gd[2]);
+    int K = 0;
+    float acc = 0.0f;
+    for (int cz = loz; cz <= hiz; cz++)
+        for (int cy = loy; cy <= hiy; cy++)
+            for (int cx = lox; cx <= hix; cx++) {
+                const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
+                const int e0 = __ldg(p.cell_start + cell), e1 = __ldg(p.cell_start + cell + 1);
+                for (int e = e0; e < e1; e++) {
+                    const int t = __ldg(p.tri_ids + e);
+                    const float4 A = __ldg(p.tri + 3 * t);
+                    const float4 B = __ldg(p.tri + 3 * t + 1);
+                    const float4 C = __ldg(p.tri + 3 * t + 2);
+                    // a triangle listed in several cells of the box is tested
+                    // only in the first cell the two boxes share
+                    if (max(__float_as_int(A.w), lox) != cx || max(__float_as_int(B.w), loy) != cy ||
+                        max(__float_as_int(C.w), loz) != cz)
+                        continue;
+                    // extended Moller-Trumbore: edge S -> E, direction r, length L
+                    const float hx = ry * C.z - rz * C.y;
+                    const float hy = rz * C.x - rx * C.z;
+                    const float hz = rx * C.y - ry * C.x;
+                    const float a = B.x * hx + B.y * hy + B.z * hz;
+                    if (fabsf(a) < p.eps) continue;
+                    const float f = 1.0f / a;
+                    const float qx0 = sx - A.x, qy0 = sy - A.y, qz0 = sz - A.z;
+                    const float u = f * (qx0 * hx + qy0 * hy + qz0 * hz);
+                    if (u < 0.0f || u > 1.0f) continue;
+                    const float qx = qy0 * B.z - qz0 * B.y;
+                    const float qy = qz0 * B.x - qx0 * B.z;
+                    const float qz = qx0 * B.y - qy0 * B.x;
+                    const float v = f * (rx * qx + ry * qy + rz * qz);
+                    const float th = f * (C.x * qx + C.y * qy + C.z * qz);
+                    if (v < 0.0f || u + v > 1.0f) continue;
+                    if (!(th > p.tmin && th < L)) continue;
+                    K++;
+                    acc += fmaxf(th - p.delta, 0.0f);
+                }
+            }
+    if (K == 0) return false;
+    const float m = acc / (float)K;
+    ox = sx + m * rx;
+    oy = sy + m * ry;
+    oz = sz + m * rz;
+    return true;
 }
 
 template <bool MESH, bool PER_SPRING>
-__global__ void __launch_bounds__(NTHREADS) substep_kernel(const StepParams p)
+__global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) substep_kernel(const StepParams p)
 {
-    constexpr int DR[CLOTH_NDIR] = {0, 1, 1, 1, 0, 2};
-    constexpr int DC[CLOTH_NDIR] = {1, 0, 1, -1, 2, 0};
-    constexpr int TYPE[CLOTH_NDIR] = {0, 0, 1, 1, 2, 2};
-
-    __shared__ float sm[6][SY][SX];
     __shared__ unsigned long long s_k;
     __shared__ float s_wbase;
-
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    if (tid == 0) {
-        unsigned long long k = *(volatile unsigned long long *)&p.ctrl->k;
+    if (threadIdx.x == 0) {
+        const unsigned long long k = *(volatile unsigned long long *)&p.ctrl->k;
         s_k = k;
         float wb = 0.0f;
-        if (p.has_wind) {
-            // omega*k + phase0 reduced mod 2*pi in double, once per CTA
-            double ph = fmod(p.w_omega * (double)k + p.w_phase0, 6.283185307179586);
-            wb = (float)ph;
-        }
+        if (p.has_wind) wb = (float)fmod(p.w_omega * (double)k + p.w_phase0, 6.283185307179586);
         s_wbase = wb;
     }
     __syncthreads();
@@ -70,155 +184,265 @@ __global__ void __launch_bounds__(NTHREADS) substep_kernel(const StepParams p)
     const float *__restrict__ in = (k & 1ull) ? p.state1 : p.state0;
     float *__restrict__ out = (k & 1ull) ? p.state0 : p.state1;
     const long long st = p.stride;
-    const int c0 = blockIdx.x * TX, r0 = blockIdx.y * TY;
+    const int lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * WARPS_PER_CTA + (threadIdx.x >> 5);
+    float2 fsum = bc(0.0f);  // sum of every stored value: non-finite iff one of them is
 
-    for (int idx = tid; idx < SX * SY; idx += NTHREADS) {
-        int ly = idx / SX, lx = idx - ly * SX;
-        int r = r0 - HALO + ly, c = c0 - HALO + lx;
-        bool ok = (r >= 0) && (r < p.ny) && (c >= 0) && (c < p.nx);
-        long long g = (long long)r * p.nx + c;
-#pragma unroll
-        for (int q = 0; q < 6; q++) sm[q][ly][lx] = ok ? __ldg(in + q * st + g) : 0.0f;
-    }
-    __syncthreads();
+    if (warp < p.strips_x * p.strips_y) {
+        const int sx = warp % p.strips_x, sy = warp / p.strips_x;
+        const int cA = sx * STRIP_COLS - 2 + 2 * lane;  // column of node A (even)
+        const int r0 = sy * p.rows_per_warp;
+        const int r1 = min(r0 + p.rows_per_warp, p.ny);  // output rows [r0, r1)
+        const bool colmem = cA >= 0 && cA < p.pitch;     // both columns addressable
+        const bool out_lane = lane >= 1 && lane <= 30;
+        auto colok = [&](int c) { return c >= 0 && c < p.nx; };
+        // column part of the spring masks (A in .x, B in .y)
+        const float2 mR = make_float2(colok(cA) && colok(cA + 1), colok(cA + 1) && colok(cA + 2));
+        const float2 mR2 = make_float2(colok(cA) && colok(cA + 2), colok(cA + 1) && colok(cA + 3));
+        const float2 mD = make_float2(colok(cA), colok(cA + 1));
+        const float2 mDL = make_float2(colok(cA) && colok(cA - 1), colok(cA + 1) && colok(cA));
+        const bool okA = out_lane && colok(cA), okB = out_lane && colok(cA + 1);
+        // every lane's columns cA-1 .. cA+3 inside the grid
+        const bool colint = sx * STRIP_COLS - 3 >= 0 && sx * STRIP_COLS + 64 < p.nx;
 
-    bool bad = false;
-#pragma unroll 1
-    for (int jrow = 0; jrow < TY / BY; jrow++) {
-        const int ly = threadIdx.y + jrow * BY, lx = threadIdx.x;
-        const int r = r0 + ly, c = c0 + lx;
-        if (r >= p.ny || c >= p.nx) continue;
-        const int i = r * p.nx + c;
-        const int sy = ly + HALO, sx = lx + HALO;
-        const float pix = sm[0][sy][sx], piy = sm[1][sy][sx], piz = sm[2][sy][sx];
-        const float vix = sm[3][sy][sx], viy = sm[4][sy][sx], viz = sm[5][sy][sx];
-
-        float fx = 0.0f, fy = 0.0f, fz = 0.0f;
-#pragma unroll
-        for (int d = 0; d < CLOTH_NDIR; d++) {
-            // spring owned by this node, towards (+DR, +DC)
-            {
-                const int rr = r + DR[d], cc = c + DC[d];
-                if (rr < p.ny && cc >= 0 && cc < p.nx) {
-                    const float ks = PER_SPRING ? __ldg(p.ks_slot + d * st + i) : p.ks[TYPE[d]];
-                    const float kd = PER_SPRING ? __ldg(p.kd_slot + d * st + i) : p.kd[TYPE[d]];
-                    const int yy = sy + DR[d], xx = sx + DC[d];
-                    spring_add(pix, piy, piz, vix, viy, viz, sm[0][yy][xx], sm[1][yy][xx], sm[2][yy][xx],
-                               sm[3][yy][xx], sm[4][yy][xx], sm[5][yy][xx], ks, kd, p.L0[d], fx, fy, fz);
-                }
-            }
-            // spring owned by the node at (-DR, -DC), towards this node
-            {
-                const int rr = r - DR[d], cc = c - DC[d];
-                if (rr >= 0 && cc >= 0 && cc < p.nx) {
-                    const int j = i - DR[d] * p.nx - DC[d];
-                    const float ks = PER_SPRING ? __ldg(p.ks_slot + d * st + j) : p.ks[TYPE[d]];
-                    const float kd = PER_SPRING ? __ldg(p.kd_slot + d * st + j) : p.kd[TYPE[d]];
-                    const int yy = sy - DR[d], xx = sx - DC[d];
-                    spring_add(pix, piy, piz, vix, viy, viz, sm[0][yy][xx], sm[1][yy][xx], sm[2][yy][xx],
-                               sm[3][yy][xx], sm[4][yy][xx], sm[5][yy][xx], ks, kd, p.L0[d], fx, fy, fz);
-                }
-            }
+        // wind: sin(alpha_r + beta_c) with beta per column, alpha per row
+        float2 sinB = bc(0.0f), cosB = bc(0.0f);
+        float sinR = 0.0f, cosR = 0.0f, sinK = 0.0f, cosK = 1.0f;
+        if (p.has_wind) {
+            sincosf((float)cA * p.w_kc, &sinB.x, &cosB.x);
+            sincosf((float)(cA + 1) * p.w_kc, &sinB.y, &cosB.y);
+            sincosf(s_wbase + (float)(r0 - 2) * p.w_kr, &sinR, &cosR);  // the walk starts at row r0 - 2
+            sincosf(p.w_kr, &sinK, &cosK);
         }
 
-        const bool pinned = p.pin_bits && ((__ldg(p.pin_bits + (i >> 5)) >> (i & 31)) & 1u);
-        float xx_, xy_, xz_, wx, wy, wz;
-        if (pinned) {
-            xx_ = pix; xy_ = piy; xz_ = piz;
-            wx = wy = wz = 0.0f;
-        } else {
-            float ax = fx * p.inv_mass + p.g[0];
-            float ay = fy * p.inv_mass + p.g[1];
-            float az = fz * p.inv_mass + p.g[2];
-            if (p.has_wind) {
-                const float w = p.w_amp * sinf(s_wbase + (float)c * p.w_kc + (float)r * p.w_kr);
-                ax += w * p.w_dir[0];
-                ay += w * p.w_dir[1];
-                az += w * p.w_dir[2];
+        // window: rows r, r+1, r+2 of the walk, starting at r = r0 - 2
+        int r = r0 - 2;
+        Node2 P0 = load_row(in, st, p.pitch, r, p.ny, cA, colmem);
+        Node2 P1 = load_row(in, st, p.pitch, r + 1, p.ny, cA, colmem);
+        Node2 P2 = load_row(in, st, p.pitch, r + 2, p.ny, cA, colmem);
+        Node2 N0 = shfl_down_node(P0);  // lane+1's pair, row r
+        // carried spring forces (owner's forward spring; the reaction is subtracted)
+        Vec2 fD_1 = {}, fD2_1 = {}, fD2_2 = {};  // own down (r-1), down2 (r-1), down2 (r-2)
+        Vec2 bDR_1 = {}, bDL_1 = {};             // reactions of the diagonals of row r-1
+        unsigned long long markA = 0ull, markB = 0ull;  // rows whose node needs the collision phase
+
+        CLOTH_UNROLL(CLOTH_WALK_UNROLL)
+        for (; r < r1; r++) {
+            const Node2 P3 = load_row(in, st, p.pitch, r + 3, p.ny, cA, colmem);  // prefetch
+            const Node2 N1 = shfl_down_node(P1);                                  // lane+1, row r+1
+            Node2 M1;                                                             // lane-1's B, row r+1
+            M1.px.y = __shfl_up_sync(FULL, P1.px.y, 1);
+            M1.py.y = __shfl_up_sync(FULL, P1.py.y, 1);
+            M1.pz.y = __shfl_up_sync(FULL, P1.pz.y, 1);
+            M1.vx.y = __shfl_up_sync(FULL, P1.vx.y, 1);
+            M1.vy.y = __shfl_up_sync(FULL, P1.vy.y, 1);
+            M1.vz.y = __shfl_up_sync(FULL, P1.vz.y, 1);
+
+            // row masks: the spring exists when both ends are grid nodes
+            const float rr0 = (r >= 0 && r < p.ny) ? 1.0f : 0.0f;
+            const float rr1 = (r >= 0 && r + 1 < p.ny) ? 1.0f : 0.0f;
+            const float rr2 = (r >= 0 && r + 2 < p.ny) ? 1.0f : 0.0f;
+
+            float2 ksR, kdR, ksR2, kdR2, ksD, kdD, ksD2, kdD2, ksDR, kdDR, ksDL, kdDL;
+            if (PER_SPRING) {
+                // slot planes hold 0 for springs that do not exist
+                if (r >= 0 && r < p.ny && colmem) {
+                    const long long o = (long long)r * p.pitch + cA;
+                    ksR = __ldg((const float2 *)(p.ks_slot + o));
+                    kdR = __ldg((const float2 *)(p.kd_slot + o));
+                    ksD = __ldg((const float2 *)(p.ks_slot + st + o));
+                    kdD = __ldg((const float2 *)(p.kd_slot + st + o));
+                    ksDR = __ldg((const float2 *)(p.ks_slot + 2 * st + o));
+                    kdDR = __ldg((const float2 *)(p.kd_slot + 2 * st + o));
+                    ksDL = __ldg((const float2 *)(p.ks_slot + 3 * st + o));
+                    kdDL = __ldg((const float2 *)(p.kd_slot + 3 * st + o));
+                    ksR2 = __ldg((const float2 *)(p.ks_slot + 4 * st + o));
+                    kdR2 = __ldg((const float2 *)(p.kd_slot + 4 * st + o));
+                    ksD2 = __ldg((const float2 *)(p.ks_slot + 5 * st + o));
+                    kdD2 = __ldg((const float2 *)(p.kd_slot + 5 * st + o));
+                } else {
+                    ksR = kdR = ksD = kdD = ksDR = kdDR = ksDL = kdDL = ksR2 = kdR2 = ksD2 = kdD2 = bc(0.0f);
+                }
+            } else if (colint && r >= 0 && r + 2 < p.ny) {
+                // interior strip and rows: every spring exists
+                ksR = ksD = bc(p.ks[0]);
+                kdR = kdD = bc(p.kd[0]);
+                ksDR = ksDL = bc(p.ks[1]);
+                kdDR = kdDL = bc(p.kd[1]);
+                ksR2 = ksD2 = bc(p.ks[2]);
+                kdR2 = kdD2 = bc(p.kd[2]);
+            } else {
+                const float2 m0 = mul2(mR, bc(rr0)), m2 = mul2(mR2, bc(rr0));
+                const float2 mD1 = mul2(mD, bc(rr1)), mD2m = mul2(mD, bc(rr2));
+                const float2 mDR1 = mul2(mR, bc(rr1)), mDL1 = mul2(mDL, bc(rr1));
+                ksR = mul2(m0, bc(p.ks[0]));
+                kdR = mul2(m0, bc(p.kd[0]));
+                ksD = mul2(mD1, bc(p.ks[0]));
+                kdD = mul2(mD1, bc(p.kd[0]));
+                ksDR = mul2(mDR1, bc(p.ks[1]));
+                kdDR = mul2(mDR1, bc(p.kd[1]));
+                ksDL = mul2(mDL1, bc(p.ks[1]));
+                kdDL = mul2(mDL1, bc(p.kd[1]));
+                ksR2 = mul2(m2, bc(p.ks[2]));
+                kdR2 = mul2(m2, bc(p.kd[2]));
+                ksD2 = mul2(mD2m, bc(p.ks[2]));
+                kdD2 = mul2(mD2m, bc(p.kd[2]));
             }
-            wx = vix + p.dt * ax;
-            wy = viy + p.dt * ay;
-            wz = viz + p.dt * az;
-            const float ex = pix + p.dt * wx, ey = piy + p.dt * wy, ez = piz + p.dt * wz;
-            xx_ = ex; xy_ = ey; xz_ = ez;
-            if (MESH) {
-                const float dx = ex - pix, dy = ey - piy, dz = ez - piz;
-                const float L = sqrtf(dx * dx + dy * dy + dz * dz);
-                if (L >= p.eps) {
-                    const float rx = dx / L, ry = dy / L, rz = dz / L;
-                    const int lox = cell_coord(fminf(pix, ex), p.go[0], p.ginv, p.gd[0]);
-                    const int hix = cell_coord(fmaxf(pix, ex), p.go[0], p.ginv, p.gd[0]);
-                    const int loy = cell_coord(fminf(piy, ey), p.go[1], p.ginv, p.gd[1]);
-                    const int hiy = cell_coord(fmaxf(piy, ey), p.go[1], p.ginv, p.gd[1]);
-                    const int loz = cell_coord(fminf(piz, ez), p.go[2], p.ginv, p.gd[2]);
-                    const int hiz = cell_coord(fmaxf(piz, ez), p.go[2], p.ginv, p.gd[2]);
-                    int K = 0;
-                    float acc = 0.0f;
-                    for (int cz = loz; cz <= hiz; cz++)
-                        for (int cy = loy; cy <= hiy; cy++)
-                            for (int cx = lox; cx <= hix; cx++) {
-                                const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
-                                const int e0 = __ldg(p.cell_start + cell), e1 = __ldg(p.cell_start + cell + 1);
-                                for (int e = e0; e < e1; e++) {
-                                    const int t = __ldg(p.tri_ids + e);
-                                    const float4 A = __ldg(p.tri + 3 * t);
-                                    const float4 B = __ldg(p.tri + 3 * t + 1);
-                                    const float4 C = __ldg(p.tri + 3 * t + 2);
-                                    // a triangle listed in several cells of the box is
-                                    // tested only in the first cell the two boxes share
-                                    if (max(__float_as_int(A.w), lox) != cx || max(__float_as_int(B.w), loy) != cy ||
-                                        max(__float_as_int(C.w), loz) != cz)
-                                        continue;
-                                    // extended Moller-Trumbore: S = p_i, edge direction r, length L
-                                    const float hx = ry * C.z - rz * C.y;
-                                    const float hy = rz * C.x - rx * C.z;
-                                    const float hz = rx * C.y - ry * C.x;
-                                    const float a = B.x * hx + B.y * hy + B.z * hz;
-                                    if (fabsf(a) < p.eps) continue;
-                                    const float f = 1.0f / a;
-                                    const float sx_ = pix - A.x, sy_ = piy - A.y, sz_ = piz - A.z;
-                                    const float u = f * (sx_ * hx + sy_ * hy + sz_ * hz);
-                                    if (u < 0.0f || u > 1.0f) continue;
-                                    const float qx = sy_ * B.z - sz_ * B.y;
-                                    const float qy = sz_ * B.x - sx_ * B.z;
-                                    const float qz = sx_ * B.y - sy_ * B.x;
-                                    const float v = f * (rx * qx + ry * qy + rz * qz);
-                                    const float th = f * (C.x * qx + C.y * qy + C.z * qz);
-                                    if (v < 0.0f || u + v > 1.0f) continue;
-                                    if (!(th > p.tmin && th < L)) continue;
-                                    K++;
-                                    acc += fmaxf(th - p.delta, 0.0f);
-                                }
-                            }
-                    if (K > 0) {
-                        const float m = acc / (float)K;
-                        xx_ = pix + m * rx;
-                        xy_ = piy + m * ry;
-                        xz_ = piz + m * rz;
-                        wx *= p.restitution;
-                        wy *= p.restitution;
-                        wz *= p.restitution;
+
+            // the six forward springs of the pair at row r
+            Node2 Q;
+            Q.px = make_float2(P0.px.y, N0.px.x); Q.py = make_float2(P0.py.y, N0.py.x);
+            Q.pz = make_float2(P0.pz.y, N0.pz.x); Q.vx = make_float2(P0.vx.y, N0.vx.x);
+            Q.vy = make_float2(P0.vy.y, N0.vy.x); Q.vz = make_float2(P0.vz.y, N0.vz.x);
+            const Vec2 fR = spring2(P0, Q, ksR, kdR, p.L0[0]);      // (0,+1)
+            const Vec2 fR2 = spring2(P0, N0, ksR2, kdR2, p.L0[4]);  // (0,+2)
+            const Vec2 fD = spring2(P0, P1, ksD, kdD, p.L0[1]);     // (+1,0)
+            const Vec2 fD2 = spring2(P0, P2, ksD2, kdD2, p.L0[5]);  // (+2,0)
+            Q.px = make_float2(P1.px.y, N1.px.x); Q.py = make_float2(P1.py.y, N1.py.x);
+            Q.pz = make_float2(P1.pz.y, N1.pz.x); Q.vx = make_float2(P1.vx.y, N1.vx.x);
+            Q.vy = make_float2(P1.vy.y, N1.vy.x); Q.vz = make_float2(P1.vz.y, N1.vz.x);
+            const Vec2 fDR = spring2(P0, Q, ksDR, kdDR, p.L0[2]);   // (+1,+1)
+            Q.px = make_float2(M1.px.y, P1.px.x); Q.py = make_float2(M1.py.y, P1.py.x);
+            Q.pz = make_float2(M1.pz.y, P1.pz.x); Q.vx = make_float2(M1.vx.y, P1.vx.x);
+            Q.vy = make_float2(M1.vy.y, P1.vy.x); Q.vz = make_float2(M1.vz.y, P1.vz.x);
+            const Vec2 fDL = spring2(P0, Q, ksDL, kdDL, p.L0[3]);   // (+1,-1)
+
+            // reactions arriving at this row from the left neighbours' springs
+            Vec2 bR;  // right spring of (r, c-1): A <- lane-1's B, B <- own A
+            bR.x = make_float2(__shfl_up_sync(FULL, fR.x.y, 1), fR.x.x);
+            bR.y = make_float2(__shfl_up_sync(FULL, fR.y.y, 1), fR.y.x);
+            bR.z = make_float2(__shfl_up_sync(FULL, fR.z.y, 1), fR.z.x);
+            const Vec2 bR2 = {shfl_up2(fR2.x, 1), shfl_up2(fR2.y, 1), shfl_up2(fR2.z, 1)};  // (r, c-2)
+            // diagonals of this row act on row r+1: A <- lane-1's B (down-right),
+            // B <- own A; A <- own B (down-left), B <- lane+1's A
+            Vec2 nDR, nDL;
+            nDR.x = make_float2(__shfl_up_sync(FULL, fDR.x.y, 1), fDR.x.x);
+            nDR.y = make_float2(__shfl_up_sync(FULL, fDR.y.y, 1), fDR.y.x);
+            nDR.z = make_float2(__shfl_up_sync(FULL, fDR.z.y, 1), fDR.z.x);
+            nDL.x = make_float2(fDL.x.y, __shfl_down_sync(FULL, fDL.x.x, 1));
+            nDL.y = make_float2(fDL.y.y, __shfl_down_sync(FULL, fDL.y.x, 1));
+            nDL.z = make_float2(fDL.z.y, __shfl_down_sync(FULL, fDL.z.x, 1));
+
+            if (r >= r0) {
+                // F = own forward springs - reactions of the springs that end here
+                Vec2 F = vadd(vadd(vadd(fR, fR2), vadd(fD, fD2)), vadd(fDR, fDL));
+                const Vec2 back = vadd(vadd(vadd(bR, bR2), vadd(fD_1, fD2_2)), vadd(bDR_1, bDL_1));
+                F = vsub(F, back);
+
+                const long long o = (long long)r * p.pitch + cA;
+                unsigned pinw = 0u;
+                if (p.pin_bits && colmem) pinw = __ldg(p.pin_bits + (o >> 5)) >> (o & 31);
+                const bool pinA = pinw & 1u, pinB = (pinw >> 1) & 1u;
+
+                float2 ax = fma2(F.x, bc(p.inv_mass), bc(p.g[0]));
+                float2 ay = fma2(F.y, bc(p.inv_mass), bc(p.g[1]));
+                float2 az = fma2(F.z, bc(p.inv_mass), bc(p.g[2]));
+                if (p.has_wind) {
+                    // sin(alpha + beta) = sin(alpha) cos(beta) + cos(alpha) sin(beta)
+                    const float2 w = mul2(bc(p.w_amp), fma2(bc(cosR), sinB, mul2(bc(sinR), cosB)));
+                    ax = fma2(w, bc(p.w_dir[0]), ax);
+                    ay = fma2(w, bc(p.w_dir[1]), ay);
+                    az = fma2(w, bc(p.w_dir[2]), az);
+                }
+                const float2 dt = bc(p.dt);
+                float2 wx = fma2(dt, ax, P0.vx), wy = fma2(dt, ay, P0.vy), wz = fma2(dt, az, P0.vz);
+                float2 xx = fma2(dt, wx, P0.px), xy = fma2(dt, wy, P0.py), xz = fma2(dt, wz, P0.pz);
+                if (pinA) {
+                    xx.x = P0.px.x; xy.x = P0.py.x; xz.x = P0.pz.x;
+                    wx.x = wy.x = wz.x = 0.0f;
+                }
+                if (pinB) {
+                    xx.y = P0.px.y; xy.y = P0.py.y; xz.y = P0.pz.y;
+                    wx.y = wy.y = wz.y = 0.0f;
+                }
+                if (MESH) {
+                    // nodes whose path box reaches the box of the non-empty grid
+                    // cells are marked for the collision phase after the walk
+                    const bool needA = okA && !pinA && fmaxf(P0.px.x, xx.x) >= p.mlo[0] &&
+                                       fminf(P0.px.x, xx.x) <= p.mhi[0] && fmaxf(P0.py.x, xy.x) >= p.mlo[1] &&
+                                       fminf(P0.py.x, xy.x) <= p.mhi[1] && fmaxf(P0.pz.x, xz.x) >= p.mlo[2] &&
+                                       fminf(P0.pz.x, xz.x) <= p.mhi[2];
+                    const bool needB = okB && !pinB && fmaxf(P0.px.y, xx.y) >= p.mlo[0] &&
+                                       fminf(P0.px.y, xx.y) <= p.mhi[0] && fmaxf(P0.py.y, xy.y) >= p.mlo[1] &&
+                                       fminf(P0.py.y, xy.y) <= p.mhi[1] && fmaxf(P0.pz.y, xz.y) >= p.mlo[2] &&
+                                       fminf(P0.pz.y, xz.y) <= p.mhi[2];
+                    markA |= (unsigned long long)needA << (r - r0);
+                    markB |= (unsigned long long)needB << (r - r0);
+                }
+                if (okA) {
+                    if (!okB) {  // B is padding: keep it zero
+                        xx.y = xy.y = xz.y = wx.y = wy.y = wz.y = 0.0f;
                     }
+                    fsum = add2(fsum, add2(add2(add2(xx, xy), add2(xz, wx)), add2(wy, wz)));
+                    float *b = out + o;
+                    *(float2 *)(b) = xx;
+                    *(float2 *)(b + st) = xy;
+                    *(float2 *)(b + 2 * st) = xz;
+                    *(float2 *)(b + 3 * st) = wx;
+                    *(float2 *)(b + 4 * st) = wy;
+                    *(float2 *)(b + 5 * st) = wz;
+                }
+            }
+            if (p.has_wind) {  // advance the row angle by kr
+                const float s2 = sinR * cosK + cosR * sinK;
+                cosR = cosR * cosK - sinR * sinK;
+                sinR = s2;
+            }
+            // shift the window and the carried forces
+            fD2_2 = fD2_1;
+            fD2_1 = fD2;
+            fD_1 = fD;
+            bDR_1 = nDR;
+            bDL_1 = nDL;
+            P0 = P1;
+            P1 = P2;
+            P2 = P3;
+            N0 = N1;
+        }
+
+        if (MESH) {
+            // append the marked nodes to the collision list, row by row so that
+            // consecutive entries are neighbouring columns
+            const unsigned long long mine = markA | markB;
+            const unsigned lo = __reduce_or_sync(FULL, (unsigned)mine);
+            const unsigned hi = __reduce_or_sync(FULL, (unsigned)(mine >> 32));
+            unsigned long long rows = ((unsigned long long)hi << 32) | lo;
+            const int cnt = __popcll(markA) + __popcll(markB);
+            const int total = __reduce_add_sync(FULL, cnt);
+            if (total > 0) {
+                unsigned base = 0;
+                if (lane == 0) base = atomicAdd(p.coll_count, (unsigned)total);
+                base = __shfl_sync(FULL, base, 0);
+                while (rows) {
+                    const int b = __ffsll((long long)rows) - 1;
+                    rows &= rows - 1;
+                    const int a = (int)((markA >> b) & 1ull), bb = (int)((markB >> b) & 1ull);
+                    int inc = a + bb;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int y = __shfl_up_sync(FULL, inc, d);
+                        if (lane >= d) inc += y;
+                    }
+                    const int row_total = __shfl_sync(FULL, inc, 31);
+                    unsigned w = base + (unsigned)(inc - a - bb);
+                    const int o = (r0 + b) * p.pitch + cA;
+                    if (a) p.coll_list[w++] = o;
+                    if (bb) p.coll_list[w] = o + 1;
+                    base += (unsigned)row_total;
                 }
             }
         }
-        bad |= !(isfinite(xx_) && isfinite(xy_) && isfinite(xz_) && isfinite(wx) && isfinite(wy) && isfinite(wz));
-        out[0 * st + i] = xx_;
-        out[1 * st + i] = xy_;
-        out[2 * st + i] = xz_;
-        out[3 * st + i] = wx;
-        out[4 * st + i] = wy;
-        out[5 * st + i] = wz;
     }
 
-    bad = __syncthreads_or(bad);
-    if (tid == 0) {
-        if (bad) atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
+    const bool bad = !isfinite(fsum.x + fsum.y);
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
+    if (MESH) return;  // the collision kernel finishes the substep
+    __syncthreads();
+    if (threadIdx.x == 0) {
         // the last CTA to finish advances the substep counter for the next launch
         __threadfence();
-        const unsigned total = gridDim.x * gridDim.y;
         const unsigned prev = atomicAdd(&p.ctrl->blocks_done, 1u);
-        if (prev == total - 1) {
+        if (prev == gridDim.x - 1) {
             p.ctrl->blocks_done = 0;
             p.ctrl->k = k + 1;
             __threadfence();
@@ -226,41 +450,92 @@ __global__ void __launch_bounds__(NTHREADS) substep_kernel(const StepParams p)
     }
 }
 
+// Second kernel of a substep with a surface model: broad + narrow phase and
+// response of every node the walk marked (one thread per node), then the
+// substep counter advances.
+__global__ void __launch_bounds__(128, 8) collide_kernel(const StepParams p)
+{
+    __shared__ unsigned long long s_k;
+    __shared__ unsigned s_n;
+    if (threadIdx.x == 0) {
+        s_k = *(volatile unsigned long long *)&p.ctrl->k;
+        s_n = *(volatile unsigned *)p.coll_count;
+    }
+    __syncthreads();
+    const unsigned long long k = s_k;
+    const unsigned n = s_n;
+    const float *__restrict__ in = (k & 1ull) ? p.state1 : p.state0;
+    float *out = (k & 1ull) ? p.state0 : p.state1;
+    const long long st = p.stride;
+    float fsum = 0.0f;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const long long o = __ldg(p.coll_list + i);
+        const float sx = __ldg(in + o), sy = __ldg(in + st + o), sz = __ldg(in + 2 * st + o);
+        const float ex = out[o], ey = out[st + o], ez = out[2 * st + o];
+        float ox, oy, oz;
+        if (collide(p, sx, sy, sz, ex, ey, ez, ox, oy, oz)) {
+            out[o] = ox;
+            out[st + o] = oy;
+            out[2 * st + o] = oz;
+            out[3 * st + o] *= p.restitution;
+            out[4 * st + o] *= p.restitution;
+            out[5 * st + o] *= p.restitution;
+            fsum += ox + oy + oz;
+        }
+    }
+    if (__any_sync(FULL, !isfinite(fsum)) && (threadIdx.x & 31) == 0)
+        atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // the last CTA resets the list and advances the substep counter
+        __threadfence();
+        const unsigned prev = atomicAdd(&p.ctrl->blocks_done, 1u);
+        if (prev == gridDim.x - 1) {
+            p.ctrl->blocks_done = 0;
+            *p.coll_count = 0u;
+            p.ctrl->k = k + 1;
+            __threadfence();
+        }
+    }
+}
+
 __global__ void aos_to_soa_kernel(const float *__restrict__ pos, const float *__restrict__ vel, float *state0,
-                                  float *state1, long long st, int n, DevCtrl *ctrl)
+                                  float *state1, long long st, int n, int nx, int pitch, DevCtrl *ctrl)
 {
     const unsigned long long k = *(volatile unsigned long long *)&ctrl->k;
     float *dst = (k & 1ull) ? state1 : state0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const long long o = (long long)(i / nx) * pitch + (i % nx);
         if (pos) {
-            dst[0 * st + i] = pos[3 * (long long)i];
-            dst[1 * st + i] = pos[3 * (long long)i + 1];
-            dst[2 * st + i] = pos[3 * (long long)i + 2];
+            dst[0 * st + o] = pos[3 * (long long)i];
+            dst[1 * st + o] = pos[3 * (long long)i + 1];
+            dst[2 * st + o] = pos[3 * (long long)i + 2];
         }
         if (vel) {
-            dst[3 * st + i] = vel[3 * (long long)i];
-            dst[4 * st + i] = vel[3 * (long long)i + 1];
-            dst[5 * st + i] = vel[3 * (long long)i + 2];
+            dst[3 * st + o] = vel[3 * (long long)i];
+            dst[4 * st + o] = vel[3 * (long long)i + 1];
+            dst[5 * st + o] = vel[3 * (long long)i + 2];
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->flags = 0u;
 }
 
-__global__ void soa_to_aos_kernel(const float *state0, const float *state1, long long st, int n,
+__global__ void soa_to_aos_kernel(const float *state0, const float *state1, long long st, int n, int nx, int pitch,
                                   const DevCtrl *ctrl, float *__restrict__ pos, float *__restrict__ vel)
 {
     const unsigned long long k = *(volatile const unsigned long long *)&ctrl->k;
     const float *src = (k & 1ull) ? state1 : state0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const long long o = (long long)(i / nx) * pitch + (i % nx);
         if (pos) {
-            pos[3 * (long long)i] = src[0 * st + i];
-            pos[3 * (long long)i + 1] = src[1 * st + i];
-            pos[3 * (long long)i + 2] = src[2 * st + i];
+            pos[3 * (long long)i] = src[0 * st + o];
+            pos[3 * (long long)i + 1] = src[1 * st + o];
+            pos[3 * (long long)i + 2] = src[2 * st + o];
         }
         if (vel) {
-            vel[3 * (long long)i] = src[3 * st + i];
-            vel[3 * (long long)i + 1] = src[4 * st + i];
-            vel[3 * (long long)i + 2] = src[5 * st + i];
+            vel[3 * (long long)i] = src[3 * st + o];
+            vel[3 * (long long)i + 1] = src[4 * st + o];
+            vel[3 * (long long)i + 2] = src[5 * st + o];
         }
     }
 }
@@ -273,31 +548,54 @@ int transfer_blocks(int n)
 
 }  // namespace
 
+int substep_rows_per_warp(int nx, int ny, int sm_count)
+{
+    // the resident warps of one wave (register-limited), walks of 4..64 rows
+    const long long strips_x = (nx + STRIP_COLS - 1) / STRIP_COLS;
+    const long long target = (long long)sm_count * WARPS_PER_CTA * CLOTH_WALK_MINB;
+    long long strips_y = (target + strips_x - 1) / strips_x;
+    long long R = (ny + strips_y - 1) / strips_y;
+    if (R < 4) R = 4;
+    if (R > 64) R = 64;
+    return (int)R;
+}
+
+void substep_shape(StepParams &p)
+{
+    p.strips_x = (p.nx + STRIP_COLS - 1) / STRIP_COLS;
+    p.strips_y = (p.ny + p.rows_per_warp - 1) / p.rows_per_warp;
+}
+
 cudaError_t launch_substep(const StepParams &p, cudaStream_t s)
 {
-    dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY);
-    dim3 block(TX, BY);
+    const int warps = p.strips_x * p.strips_y;
+    const int blocks = (warps + WARPS_PER_CTA - 1) / WARPS_PER_CTA;
     const bool per = p.ks_slot != nullptr;
     if (p.has_mesh) {
-        if (per) substep_kernel<true, true><<<grid, block, 0, s>>>(p);
-        else substep_kernel<true, false><<<grid, block, 0, s>>>(p);
+        if (per) substep_kernel<true, true><<<blocks, 32 * WARPS_PER_CTA, 0, s>>>(p);
+        else substep_kernel<true, false><<<blocks, 32 * WARPS_PER_CTA, 0, s>>>(p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        collide_kernel<<<p.coll_blocks, 128, 0, s>>>(p);
     } else {
-        if (per) substep_kernel<false, true><<<grid, block, 0, s>>>(p);
-        else substep_kernel<false, false><<<grid, block, 0, s>>>(p);
+        if (per) substep_kernel<false, true><<<blocks, 32 * WARPS_PER_CTA, 0, s>>>(p);
+        else substep_kernel<false, false><<<blocks, 32 * WARPS_PER_CTA, 0, s>>>(p);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_aos_to_soa(const float *aos_pos, const float *aos_vel, float *state0, float *state1,
-                              long long stride, int n, DevCtrl *ctrl, cudaStream_t s)
+                              long long stride, int n, int nx, int pitch, DevCtrl *ctrl, cudaStream_t s)
 {
-    aos_to_soa_kernel<<<transfer_blocks(n), 256, 0, s>>>(aos_pos, aos_vel, state0, state1, stride, n, ctrl);
+    aos_to_soa_kernel<<<transfer_blocks(n), 256, 0, s>>>(aos_pos, aos_vel, state0, state1, stride, n, nx, pitch,
+                                                         ctrl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_soa_to_aos(const float *state0, const float *state1, long long stride, int n,
+cudaError_t launch_soa_to_aos(const float *state0, const float *state1, long long stride, int n, int nx, int pitch,
                               const DevCtrl *ctrl, float *aos_pos, float *aos_vel, cudaStream_t s)
 {
-    soa_to_aos_kernel<<<transfer_blocks(n), 256, 0, s>>>(state0, state1, stride, n, ctrl, aos_pos, aos_vel);
+    soa_to_aos_kernel<<<transfer_blocks(n), 256, 0, s>>>(state0, state1, stride, n, nx, pitch, ctrl, aos_pos,
+                                                         aos_vel);
     return cudaGetLastError();
 }

@@ -50,11 +50,12 @@ def test_struct_layout_matches_c(capi, tmp_path):
 #include "cloth.h"
 #define F(T, m) printf(#T "." #m " %zu\n", offsetof(T, m))
 int main(void) {
-  printf("ClothDesc %zu\nClothWind %zu\nClothInfo %zu\n", sizeof(ClothDesc), sizeof(ClothWind), sizeof(ClothInfo));
+  printf("ClothDesc %zu\nClothWind %zu\nClothInfo %zu\nClothGridParams %zu\n", sizeof(ClothDesc), sizeof(ClothWind), sizeof(ClothInfo), sizeof(ClothGridParams));
   F(ClothDesc, ks_spring); F(ClothDesc, pinned); F(ClothDesc, gravity); F(ClothDesc, dt);
   F(ClothDesc, substeps); F(ClothDesc, mt_t_min); F(ClothDesc, wind); F(ClothDesc, flags);
   F(ClothInfo, substeps_done); F(ClothInfo, pos_planes); F(ClothInfo, vel_planes); F(ClothInfo, ntris);
-  F(ClothInfo, grid_h); F(ClothInfo, grid_entries); F(ClothInfo, has_per_spring);
+  F(ClothInfo, grid_h); F(ClothInfo, grid_entries); F(ClothInfo, has_per_spring); F(ClothInfo, row_pitch);
+  F(ClothGridParams, origin); F(ClothGridParams, dims); F(ClothGridParams, ncells); F(ClothGridParams, nentries);
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -64,6 +65,7 @@ int main(void) {
     assert int(got["ClothDesc"]) == C.sizeof(capi.ClothDesc)
     assert int(got["ClothWind"]) == C.sizeof(capi.ClothWind)
     assert int(got["ClothInfo"]) == C.sizeof(capi.ClothInfo)
+    assert int(got["ClothGridParams"]) == C.sizeof(capi.ClothGridParams)
     for key, val in got.items():
         if "." in key:
             T, m = key.split(".")
