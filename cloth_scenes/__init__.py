@@ -20,6 +20,7 @@ collision experiments (Section 4.1, 4.2) at the resolutions the workloads name.
 from __future__ import annotations
 
 import dataclasses
+import functools
 import math
 from typing import List, Optional, Tuple
 
@@ -67,7 +68,14 @@ def icosphere(level: int) -> Tuple[np.ndarray, np.ndarray]:
 
     Returns (verts float64 (10*4^L+2, 3), tris int32 (20*4^L, 3)); faces are
     oriented outward and each face of level L-1 becomes 4 consecutive faces.
+    (Cached per level; callers get copies.)
     """
+    v, f = _icosphere_cached(int(level))
+    return v.copy(), f.copy()
+
+
+@functools.lru_cache(maxsize=None)
+def _icosphere_cached(level: int) -> Tuple[np.ndarray, np.ndarray]:
     v, f = _icosahedron()
     verts = [tuple(x) for x in v]
     for _ in range(level):

@@ -181,6 +181,49 @@ int cloth_get_grid(ClothHandle *h, int32_t *cell_start, int32_t *tri_ids);
 int cloth_query_candidates(ClothHandle *h, const float *S, const float *E, int32_t nseg,
                            int32_t *counts, int32_t *ids, int32_t cap);
 
+/* ---- batches of cloths ------------------------------------------------- */
+
+/* Many independent cloths (each with its own grid, constants, pins and
+ * surface model) stepped together: every substep is one persistent walk
+ * launch over a (cloth, strip) work list sorted longest first plus one
+ * collision launch over the nodes of all cloths near their meshes, replayed
+ * from a CUDA graph holding one step.  Each cloth gets exactly the arithmetic
+ * it gets from cloth_step (bitwise the same results).  Not in the paper. */
+typedef struct ClothBatch ClothBatch;
+
+typedef struct ClothBatchTuning {
+    int32_t rows_per_warp;     /* strip height of one warp's walk */
+    int32_t walk_ctas_per_sm;  /* persistent walk grid = SMs x this */
+    float us_per_substep;      /* measured by cloth_batch_tune (0 otherwise) */
+    int32_t candidates;        /* configurations timed by cloth_batch_tune */
+} ClothBatchTuning;
+
+/* count descriptions (all with the same dt and substeps), each validated and
+ * copied as by cloth_create; all work runs on stream. */
+int cloth_batch_create(const ClothDesc *descs, int32_t count, void *stream, ClothBatch **out);
+/* cloth_set_mesh for cloth `index` of the batch.  Synchronises. */
+int cloth_batch_set_mesh(ClothBatch *b, int32_t index, const float *verts, int32_t nverts, const int32_t *tris,
+                         int32_t ntris);
+/* Enqueue nsteps steps of every cloth. */
+int cloth_batch_step(ClothBatch *b, int32_t nsteps);
+/* cloth_read for cloth `index`.  Synchronises; CLOTH_ERR_NONFINITE if any
+ * cloth of the batch became non-finite. */
+int cloth_batch_read(ClothBatch *b, int32_t index, float *pos_out, float *vel_out);
+/* cloth_set_state for cloth `index` (clears the batch's non-finite flag). */
+int cloth_batch_set_state(ClothBatch *b, int32_t index, const float *pos, const float *vel);
+/* Autotuner: times trial_substeps substeps of the batch for every candidate
+ * (rows_per_warp in {4,6,8,12,16,24,32} x walk CTAs per SM), keeps the
+ * fastest, and restores every cloth's state and the substep counter, so the
+ * simulation is unchanged.  Synchronises. */
+int cloth_batch_tune(ClothBatch *b, int32_t trial_substeps, ClothBatchTuning *out);
+/* Set the tuning explicitly (rows_per_warp 1..64, walk_ctas_per_sm 1..32). */
+int cloth_batch_set_tuning(ClothBatch *b, int32_t rows_per_warp, int32_t walk_ctas_per_sm);
+int cloth_batch_get_tuning(ClothBatch *b, ClothBatchTuning *out);
+/* Wait for the batch's stream and report device-side error flags. */
+int cloth_batch_sync(ClothBatch *b);
+/* Release the batch and its cloths.  NULL-safe. */
+void cloth_batch_destroy(ClothBatch *b);
+
 /* ---- allocation-free grid build --------------------------------------- */
 
 /* Largest mesh and grid cloth_grid_build_static accepts. */

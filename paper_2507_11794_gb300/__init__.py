@@ -23,7 +23,7 @@ import numpy as np
 from . import capi
 from .capi import ClothError
 
-__all__ = ["Cloth", "ClothError", "capi", "make_desc", "current_stream"]
+__all__ = ["Cloth", "ClothBatch", "ClothError", "capi", "make_desc", "current_stream"]
 
 
 def current_stream() -> int:
@@ -122,6 +122,61 @@ class Cloth:
     def close(self):
         if getattr(self, "h", None):
             capi.cloth_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class ClothBatch:
+    """Many independent cloths stepped together (owner of a ClothBatch)."""
+
+    def __init__(self, problems, stream: int | None = None, flags: int = 0, mesh: bool = True):
+        keep: list = []
+        descs = [make_desc(p, keep, flags) for p in problems]
+        self.sizes = [d.nx * d.ny for d in descs]
+        self.h = capi.cloth_batch_create(descs, current_stream() if stream is None else stream)
+        if mesh:
+            for i, p in enumerate(problems):
+                if getattr(p, "mesh_tris", None) is not None and len(p.mesh_tris):
+                    capi.cloth_batch_set_mesh(self.h, i, p.mesh_verts, p.mesh_tris)
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def step(self, nsteps: int = 1):
+        capi.cloth_batch_step(self.h, nsteps)
+
+    def read(self, index: int, pos=True, vel=True):
+        return capi.cloth_batch_read(self.h, index, self.sizes[index], pos, vel)
+
+    def set_state(self, index: int, pos=None, vel=None):
+        capi.cloth_batch_set_state(self.h, index, pos, vel)
+
+    def tune(self, trial_substeps: int = 20):
+        return capi.cloth_batch_tune(self.h, trial_substeps)
+
+    def set_tuning(self, rows_per_warp: int, walk_ctas_per_sm: int):
+        capi.cloth_batch_set_tuning(self.h, rows_per_warp, walk_ctas_per_sm)
+
+    def tuning(self):
+        return capi.cloth_batch_get_tuning(self.h)
+
+    def sync(self):
+        capi.cloth_batch_sync(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            capi.cloth_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -33,7 +33,10 @@ _NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5
 # Every symbol include/cloth.h declares (checked by the CPU test-suite).
 EXPORTS = ("cloth_create", "cloth_set_mesh", "cloth_step", "cloth_read", "cloth_destroy",
            "cloth_set_state", "cloth_sync", "cloth_last_error", "cloth_get_info", "cloth_get_grid",
-           "cloth_query_candidates", "cloth_grid_build_static")
+           "cloth_query_candidates", "cloth_grid_build_static",
+           "cloth_batch_create", "cloth_batch_set_mesh", "cloth_batch_step", "cloth_batch_read",
+           "cloth_batch_set_state", "cloth_batch_tune", "cloth_batch_set_tuning", "cloth_batch_get_tuning",
+           "cloth_batch_sync", "cloth_batch_destroy")
 
 
 class ClothError(RuntimeError):
@@ -81,6 +84,11 @@ class ClothGridParams(C.Structure):
                 ("ncells", C.c_int64), ("nentries", C.c_int64)]
 
 
+class ClothBatchTuning(C.Structure):
+    _fields_ = [("rows_per_warp", C.c_int32), ("walk_ctas_per_sm", C.c_int32), ("us_per_substep", C.c_float),
+                ("candidates", C.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -112,9 +120,20 @@ def lib():
         L.cloth_query_candidates.argtypes = [H, fp, fp, C.c_int32, ip, ip, C.c_int32]
         L.cloth_grid_build_static.argtypes = [fp, C.c_int32, ip, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_int64, C.c_void_p, C.c_int64, C.POINTER(ClothGridParams)]
+        L.cloth_batch_create.argtypes = [C.POINTER(ClothDesc), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]
+        L.cloth_batch_set_mesh.argtypes = [H, C.c_int32, fp, C.c_int32, ip, C.c_int32]
+        L.cloth_batch_step.argtypes = [H, C.c_int32]
+        L.cloth_batch_read.argtypes = [H, C.c_int32, fp, fp]
+        L.cloth_batch_set_state.argtypes = [H, C.c_int32, fp, fp]
+        L.cloth_batch_tune.argtypes = [H, C.c_int32, C.POINTER(ClothBatchTuning)]
+        L.cloth_batch_set_tuning.argtypes = [H, C.c_int32, C.c_int32]
+        L.cloth_batch_get_tuning.argtypes = [H, C.POINTER(ClothBatchTuning)]
+        L.cloth_batch_sync.argtypes = [H]
+        L.cloth_batch_destroy.argtypes = [H]
+        L.cloth_batch_destroy.restype = None
         for name in EXPORTS:
             f = getattr(L, name)
-            if name not in ("cloth_destroy", "cloth_last_error"):
+            if name not in ("cloth_destroy", "cloth_last_error", "cloth_batch_destroy"):
                 f.restype = C.c_int
         _lib = L
         return L
@@ -222,3 +241,59 @@ def cloth_grid_build_static(verts, tris, stream, d_tri_records, d_cell_start, ce
                                        C.c_void_p(d_tri_records), C.c_void_p(d_cell_start), int(cell_capacity),
                                        C.c_void_p(d_tri_ids), int(entry_capacity), C.byref(prm))
     return rc, prm
+
+
+# ---------------------------------------------------------------- batches
+
+def cloth_batch_create(descs, stream: int = 0) -> int:
+    arr = (ClothDesc * len(descs))(*descs)
+    h = C.c_void_p()
+    check(lib().cloth_batch_create(arr, len(descs), C.c_void_p(stream), C.byref(h)))
+    return h.value
+
+
+def cloth_batch_set_mesh(b: int, index: int, verts, tris):
+    v = None if verts is None else f32(verts, (-1, 3))
+    t = None if tris is None else np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+    check(lib().cloth_batch_set_mesh(b, int(index), _fp(v), 0 if v is None else len(v), _ip(t),
+                                     0 if t is None else len(t)))
+
+
+def cloth_batch_step(b: int, nsteps: int):
+    check(lib().cloth_batch_step(b, int(nsteps)))
+
+
+def cloth_batch_read(b: int, index: int, n: int, pos=True, vel=True):
+    p = np.empty((n, 3), np.float32) if pos else None
+    v = np.empty((n, 3), np.float32) if vel else None
+    check(lib().cloth_batch_read(b, int(index), _fp(p), _fp(v)))
+    return p, v
+
+
+def cloth_batch_set_state(b: int, index: int, pos=None, vel=None):
+    check(lib().cloth_batch_set_state(b, int(index), _fp(f32(pos)), _fp(f32(vel))))
+
+
+def cloth_batch_tune(b: int, trial_substeps: int = 20) -> ClothBatchTuning:
+    t = ClothBatchTuning()
+    check(lib().cloth_batch_tune(b, int(trial_substeps), C.byref(t)))
+    return t
+
+
+def cloth_batch_set_tuning(b: int, rows_per_warp: int, walk_ctas_per_sm: int):
+    check(lib().cloth_batch_set_tuning(b, int(rows_per_warp), int(walk_ctas_per_sm)))
+
+
+def cloth_batch_get_tuning(b: int) -> ClothBatchTuning:
+    t = ClothBatchTuning()
+    check(lib().cloth_batch_get_tuning(b, C.byref(t)))
+    return t
+
+
+def cloth_batch_sync(b: int):
+    check(lib().cloth_batch_sync(b))
+
+
+def cloth_batch_destroy(b: int):
+    if b:
+        lib().cloth_batch_destroy(b)

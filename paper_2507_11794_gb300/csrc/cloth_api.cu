@@ -11,28 +11,6 @@
 
 #include "cloth_internal.h"
 
-struct ClothHandle {
-    ClothDesc desc;  // array pointers cleared after the copy
-    int n = 0;
-    int pitch = 0;           // floats per row: nx rounded up to 4
-    int sm_count = 0;
-    long long stride = 0;
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    float *state = nullptr;  // 2 buffers x 6 planes x stride
-    uint32_t *pin_bits = nullptr;
-    float *ks_slot = nullptr, *kd_slot = nullptr;
-    DevCtrl *ctrl = nullptr;
-    float *staging = nullptr;  // 6*n floats for AoS transfers
-    int *coll_list = nullptr;  // n entries
-    DevGrid grid{};
-    bool has_mesh = false;
-    StepParams params{};
-    cudaGraphExec_t graph = nullptr;
-    long long substeps_done = 0;
-    bool dead = false;
-};
 
 namespace {
 
@@ -100,6 +78,8 @@ void free_all(ClothHandle *h)
     cudaFree(h->staging);
     cudaFree(h->coll_list);
     h->coll_list = nullptr;
+    cudaFree(h->wind_tab);
+    h->wind_tab = nullptr;
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->state = nullptr;
     h->pin_bits = nullptr;
@@ -109,7 +89,10 @@ void free_all(ClothHandle *h)
     h->cap_stream = nullptr;
 }
 
-void fill_params(ClothHandle *h)
+}  // namespace
+
+// Derives the kernel parameters from the handle's description and buffers.
+void cloth_fill_params(ClothHandle *h)
 {
     const ClothDesc &d = h->desc;
     StepParams &p = h->params;
@@ -156,6 +139,8 @@ void fill_params(ClothHandle *h)
     p.w_phase0 = fmod((double)d.wind.phase + (double)d.wind.kappa * k0, two_pi);
     p.w_kc = (float)((double)d.wind.kappa * kc);
     p.w_kr = (float)((double)d.wind.kappa * kr);
+    p.wind_rows = h->wind_tab;
+    p.wind_cols = h->wind_tab ? h->wind_tab + d.ny : nullptr;
     p.has_mesh = h->has_mesh;
     p.tri = h->grid.tri;
     p.cell_start = h->grid.cell_start;
@@ -181,6 +166,8 @@ void fill_params(ClothHandle *h)
     p.coll_count = h->ctrl ? &h->ctrl->coll_count : nullptr;
     p.coll_blocks = h->sm_count * 8;
 }
+
+namespace {
 
 void invalidate_graph(ClothHandle *h)
 {
@@ -336,6 +323,22 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
                     break;
             }
         }
+        if (d.wind.amp != 0.0f) {
+            // (sin, cos) of kappa*(udir.dv)*row and kappa*(udir.du)*col, in double
+            double kc = 0.0, kr = 0.0;
+            for (int a = 0; a < 3; a++) {
+                kc += (double)d.wind.udir[a] * d.du[a];
+                kr += (double)d.wind.udir[a] * d.dv[a];
+            }
+            kc *= d.wind.kappa;
+            kr *= d.wind.kappa;
+            std::vector<float2> tab((size_t)d.ny + d.nx);
+            for (long long r = 0; r < d.ny; r++) tab[r] = make_float2((float)sin(kr * r), (float)cos(kr * r));
+            for (long long c = 0; c < d.nx; c++)
+                tab[d.ny + c] = make_float2((float)sin(kc * c), (float)cos(kc * c));
+            if ((e = cudaMalloc(&h->wind_tab, sizeof(float2) * tab.size())) != cudaSuccess) break;
+            if ((e = upload(h->wind_tab, tab.data(), sizeof(float2) * tab.size(), h->stream)) != cudaSuccess) break;
+        }
         if (d.ks_spring || d.kd_spring) {
             // canonical order -> [direction][owner node] slots
             std::vector<float> ks(6 * (size_t)h->stride, 0.0f), kd(6 * (size_t)h->stride, 0.0f);
@@ -372,7 +375,7 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
         cudaGetLastError();
         return rc;
     }
-    fill_params(h);
+    cloth_fill_params(h);
     *out = h;
     return CLOTH_OK;
 }
@@ -416,7 +419,7 @@ int cloth_set_mesh(ClothHandle *h, const float *verts, int32_t nverts, const int
     grid_free(&h->grid);
     h->grid = g;
     h->has_mesh = ntris > 0;
-    fill_params(h);
+    cloth_fill_params(h);
     invalidate_graph(h);
     return CLOTH_OK;
 }

@@ -42,6 +42,8 @@ struct StepParams {
     float w_amp, w_dir[3];
     double w_omega, w_phase0;
     float w_kc, w_kr;
+    const float2 *wind_rows;   // (sin, cos) of row*kr per row
+    const float2 *wind_cols;   // (sin, cos) of col*kc per column
     // surface model
     int has_mesh;
     const float4 *tri;         // 3 float4 per triangle: (v0, lo.x) (e1, lo.y) (e2, lo.z)
@@ -52,6 +54,7 @@ struct StepParams {
     int gd[3];
     float mlo[3], mhi[3];      // box of the grid's non-border cells (early out)
     int *coll_list;            // node offsets marked for the collision kernel (capacity N)
+    int *coll_cloth;           // batch mode: cloth index of each entry (nullptr for one cloth)
     unsigned *coll_count;      // entries in coll_list (reset by the collision kernel)
     int coll_blocks;           // CTAs of the collision kernel
     float delta, eps, tmin, restitution;
@@ -60,6 +63,22 @@ struct StepParams {
 
 // Launch one substep (reads state k&1, writes the other, advances ctrl->k).
 cudaError_t launch_substep(const StepParams &p, cudaStream_t s);
+
+// A batch of cloths stepped by one persistent walk launch per substep.
+struct BatchArgs {
+    const StepParams *params;  // one per cloth (device)
+    const int4 *items;         // (cloth, strip x, strip y, cost), longest first
+    int n_items;
+    unsigned *work;            // next item (re-armed by the last CTA)
+    DevCtrl *ctrl;             // shared substep counter and flags
+    int *coll_list, *coll_cloth;
+    unsigned *coll_count;
+    int walk_blocks, coll_blocks;
+};
+cudaError_t launch_batch_substep(const BatchArgs &b, cudaStream_t s);
+int substep_strip_cols();
+int substep_warps_per_cta();
+int substep_min_ctas();
 // Rows per warp of the column walk for a grid and SM count; strips from it.
 int substep_rows_per_warp(int nx, int ny, int sm_count);
 void substep_shape(StepParams &p);
@@ -120,3 +139,30 @@ cudaError_t grid_build_noalloc(const float *d_verts, const int *d_tris, int nt, 
 
 // Sets the calling thread's cloth_last_error() message.
 void cloth_set_error_message(const char *msg);
+
+// One cloth (the opaque handle of the C ABI).
+struct ClothHandle {
+    ClothDesc desc;  // array pointers cleared after the copy
+    int n = 0;
+    int pitch = 0;           // floats per row: nx rounded up to 4
+    int sm_count = 0;
+    long long stride = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    float *state = nullptr;  // 2 buffers x 6 planes x stride
+    uint32_t *pin_bits = nullptr;
+    float *ks_slot = nullptr, *kd_slot = nullptr;
+    DevCtrl *ctrl = nullptr;
+    float *staging = nullptr;  // 6*n floats for AoS transfers
+    int *coll_list = nullptr;  // n entries
+    float2 *wind_tab = nullptr; // ny row entries then nx column entries
+    DevGrid grid{};
+    bool has_mesh = false;
+    StepParams params{};
+    cudaGraphExec_t graph = nullptr;
+    long long substeps_done = 0;
+    bool dead = false;
+};
+
+void cloth_fill_params(ClothHandle *h);

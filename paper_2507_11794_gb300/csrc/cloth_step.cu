@@ -167,6 +167,271 @@ __device__ __forceinline__ bool collide(const StepParams &p, float sx, float sy,
     return true;
 }
 
+// One warp's strip: columns [60 sx - 2, 60 sx + 62) walked down rows
+// [r0 - 2, r0 + rows_per_warp); writes rows [r0, r1) of the output state and,
+// with a surface model, appends the nodes that need the collision kernel.
+template <bool MESH, bool PER_SPRING>
+__device__ __forceinline__ void walk_strip(const StepParams &p, const float *__restrict__ in, float *__restrict__ out,
+                                           float wbase, int sx, int sy, int lane, int cloth, float2 &fsum)
+{
+    const long long st = p.stride;
+    const int cA = sx * STRIP_COLS - 2 + 2 * lane;  // column of node A (even)
+    const int r0 = sy * p.rows_per_warp;
+    const int r1 = min(r0 + p.rows_per_warp, p.ny);  // output rows [r0, r1)
+    const bool colmem = cA >= 0 && cA < p.pitch;     // both columns addressable
+    const bool out_lane = lane >= 1 && lane <= 30;
+    auto colok = [&](int c) { return c >= 0 && c < p.nx; };
+    // column part of the spring masks (A in .x, B in .y)
+    const float2 mR = make_float2(colok(cA) && colok(cA + 1), colok(cA + 1) && colok(cA + 2));
+    const float2 mR2 = make_float2(colok(cA) && colok(cA + 2), colok(cA + 1) && colok(cA + 3));
+    const float2 mD = make_float2(colok(cA), colok(cA + 1));
+    const float2 mDL = make_float2(colok(cA) && colok(cA - 1), colok(cA + 1) && colok(cA));
+    const bool okA = out_lane && colok(cA), okB = out_lane && colok(cA + 1);
+    // every lane's columns cA-1 .. cA+3 inside the grid
+    const bool colint = sx * STRIP_COLS - 3 >= 0 && sx * STRIP_COLS + 64 < p.nx;
+
+    // wind: sin(base + alpha_r + beta_c) from per-row and per-column tables of
+    // (sin, cos) and the addition formula; depends only on (row, col, time)
+    float2 sinB = bc(0.0f), cosB = bc(0.0f);
+    float sinW = 0.0f, cosW = 1.0f;
+    if (p.has_wind) {
+        if (cA >= 0 && cA < p.nx) {
+            const float2 t = __ldg(p.wind_cols + cA);
+            sinB.x = t.x;
+            cosB.x = t.y;
+        }
+        if (cA + 1 >= 0 && cA + 1 < p.nx) {
+            const float2 t = __ldg(p.wind_cols + cA + 1);
+            sinB.y = t.x;
+            cosB.y = t.y;
+        }
+        sincosf(wbase, &sinW, &cosW);
+    }
+
+    // window: rows r, r+1, r+2 of the walk, starting at r = r0 - 2
+    int r = r0 - 2;
+    Node2 P0 = load_row(in, st, p.pitch, r, p.ny, cA, colmem);
+    Node2 P1 = load_row(in, st, p.pitch, r + 1, p.ny, cA, colmem);
+    Node2 P2 = load_row(in, st, p.pitch, r + 2, p.ny, cA, colmem);
+    Node2 N0 = shfl_down_node(P0);  // lane+1's pair, row r
+    // carried spring forces (owner's forward spring; the reaction is subtracted)
+    Vec2 fD_1 = {}, fD2_1 = {}, fD2_2 = {};  // own down (r-1), down2 (r-1), down2 (r-2)
+    Vec2 bDR_1 = {}, bDL_1 = {};             // reactions of the diagonals of row r-1
+    unsigned long long markA = 0ull, markB = 0ull;  // rows whose node needs the collision phase
+
+    CLOTH_UNROLL(CLOTH_WALK_UNROLL)
+    for (; r < r1; r++) {
+        const Node2 P3 = load_row(in, st, p.pitch, r + 3, p.ny, cA, colmem);  // prefetch
+        const Node2 N1 = shfl_down_node(P1);                                  // lane+1, row r+1
+        Node2 M1;                                                             // lane-1's B, row r+1
+        M1.px.y = __shfl_up_sync(FULL, P1.px.y, 1);
+        M1.py.y = __shfl_up_sync(FULL, P1.py.y, 1);
+        M1.pz.y = __shfl_up_sync(FULL, P1.pz.y, 1);
+        M1.vx.y = __shfl_up_sync(FULL, P1.vx.y, 1);
+        M1.vy.y = __shfl_up_sync(FULL, P1.vy.y, 1);
+        M1.vz.y = __shfl_up_sync(FULL, P1.vz.y, 1);
+
+        // row masks: the spring exists when both ends are grid nodes
+        const float rr0 = (r >= 0 && r < p.ny) ? 1.0f : 0.0f;
+        const float rr1 = (r >= 0 && r + 1 < p.ny) ? 1.0f : 0.0f;
+        const float rr2 = (r >= 0 && r + 2 < p.ny) ? 1.0f : 0.0f;
+
+        float2 ksR, kdR, ksR2, kdR2, ksD, kdD, ksD2, kdD2, ksDR, kdDR, ksDL, kdDL;
+        if (PER_SPRING) {
+            // slot planes hold 0 for springs that do not exist
+            if (r >= 0 && r < p.ny && colmem) {
+                const long long o = (long long)r * p.pitch + cA;
+                ksR = __ldg((const float2 *)(p.ks_slot + o));
+                kdR = __ldg((const float2 *)(p.kd_slot + o));
+                ksD = __ldg((const float2 *)(p.ks_slot + st + o));
+                kdD = __ldg((const float2 *)(p.kd_slot + st + o));
+                ksDR = __ldg((const float2 *)(p.ks_slot + 2 * st + o));
+                kdDR = __ldg((const float2 *)(p.kd_slot + 2 * st + o));
+                ksDL = __ldg((const float2 *)(p.ks_slot + 3 * st + o));
+                kdDL = __ldg((const float2 *)(p.kd_slot + 3 * st + o));
+                ksR2 = __ldg((const float2 *)(p.ks_slot + 4 * st + o));
+                kdR2 = __ldg((const float2 *)(p.kd_slot + 4 * st + o));
+                ksD2 = __ldg((const float2 *)(p.ks_slot + 5 * st + o));
+                kdD2 = __ldg((const float2 *)(p.kd_slot + 5 * st + o));
+            } else {
+                ksR = kdR = ksD = kdD = ksDR = kdDR = ksDL = kdDL = ksR2 = kdR2 = ksD2 = kdD2 = bc(0.0f);
+            }
+        } else if (colint && r >= 0 && r + 2 < p.ny) {
+            // interior strip and rows: every spring exists
+            ksR = ksD = bc(p.ks[0]);
+            kdR = kdD = bc(p.kd[0]);
+            ksDR = ksDL = bc(p.ks[1]);
+            kdDR = kdDL = bc(p.kd[1]);
+            ksR2 = ksD2 = bc(p.ks[2]);
+            kdR2 = kdD2 = bc(p.kd[2]);
+        } else {
+            const float2 m0 = mul2(mR, bc(rr0)), m2 = mul2(mR2, bc(rr0));
+            const float2 mD1 = mul2(mD, bc(rr1)), mD2m = mul2(mD, bc(rr2));
+            const float2 mDR1 = mul2(mR, bc(rr1)), mDL1 = mul2(mDL, bc(rr1));
+            ksR = mul2(m0, bc(p.ks[0]));
+            kdR = mul2(m0, bc(p.kd[0]));
+            ksD = mul2(mD1, bc(p.ks[0]));
+            kdD = mul2(mD1, bc(p.kd[0]));
+            ksDR = mul2(mDR1, bc(p.ks[1]));
+            kdDR = mul2(mDR1, bc(p.kd[1]));
+            ksDL = mul2(mDL1, bc(p.ks[1]));
+            kdDL = mul2(mDL1, bc(p.kd[1]));
+            ksR2 = mul2(m2, bc(p.ks[2]));
+            kdR2 = mul2(m2, bc(p.kd[2]));
+            ksD2 = mul2(mD2m, bc(p.ks[2]));
+            kdD2 = mul2(mD2m, bc(p.kd[2]));
+        }
+
+        // the six forward springs of the pair at row r
+        Node2 Q;
+        Q.px = make_float2(P0.px.y, N0.px.x); Q.py = make_float2(P0.py.y, N0.py.x);
+        Q.pz = make_float2(P0.pz.y, N0.pz.x); Q.vx = make_float2(P0.vx.y, N0.vx.x);
+        Q.vy = make_float2(P0.vy.y, N0.vy.x); Q.vz = make_float2(P0.vz.y, N0.vz.x);
+        const Vec2 fR = spring2(P0, Q, ksR, kdR, p.L0[0]);      // (0,+1)
+        const Vec2 fR2 = spring2(P0, N0, ksR2, kdR2, p.L0[4]);  // (0,+2)
+        const Vec2 fD = spring2(P0, P1, ksD, kdD, p.L0[1]);     // (+1,0)
+        const Vec2 fD2 = spring2(P0, P2, ksD2, kdD2, p.L0[5]);  // (+2,0)
+        Q.px = make_float2(P1.px.y, N1.px.x); Q.py = make_float2(P1.py.y, N1.py.x);
+        Q.pz = make_float2(P1.pz.y, N1.pz.x); Q.vx = make_float2(P1.vx.y, N1.vx.x);
+        Q.vy = make_float2(P1.vy.y, N1.vy.x); Q.vz = make_float2(P1.vz.y, N1.vz.x);
+        const Vec2 fDR = spring2(P0, Q, ksDR, kdDR, p.L0[2]);   // (+1,+1)
+        Q.px = make_float2(M1.px.y, P1.px.x); Q.py = make_float2(M1.py.y, P1.py.x);
+        Q.pz = make_float2(M1.pz.y, P1.pz.x); Q.vx = make_float2(M1.vx.y, P1.vx.x);
+        Q.vy = make_float2(M1.vy.y, P1.vy.x); Q.vz = make_float2(M1.vz.y, P1.vz.x);
+        const Vec2 fDL = spring2(P0, Q, ksDL, kdDL, p.L0[3]);   // (+1,-1)
+
+        // reactions arriving at this row from the left neighbours' springs
+        Vec2 bR;  // right spring of (r, c-1): A <- lane-1's B, B <- own A
+        bR.x = make_float2(__shfl_up_sync(FULL, fR.x.y, 1), fR.x.x);
+        bR.y = make_float2(__shfl_up_sync(FULL, fR.y.y, 1), fR.y.x);
+        bR.z = make_float2(__shfl_up_sync(FULL, fR.z.y, 1), fR.z.x);
+        const Vec2 bR2 = {shfl_up2(fR2.x, 1), shfl_up2(fR2.y, 1), shfl_up2(fR2.z, 1)};  // (r, c-2)
+        // diagonals of this row act on row r+1: A <- lane-1's B (down-right),
+        // B <- own A; A <- own B (down-left), B <- lane+1's A
+        Vec2 nDR, nDL;
+        nDR.x = make_float2(__shfl_up_sync(FULL, fDR.x.y, 1), fDR.x.x);
+        nDR.y = make_float2(__shfl_up_sync(FULL, fDR.y.y, 1), fDR.y.x);
+        nDR.z = make_float2(__shfl_up_sync(FULL, fDR.z.y, 1), fDR.z.x);
+        nDL.x = make_float2(fDL.x.y, __shfl_down_sync(FULL, fDL.x.x, 1));
+        nDL.y = make_float2(fDL.y.y, __shfl_down_sync(FULL, fDL.y.x, 1));
+        nDL.z = make_float2(fDL.z.y, __shfl_down_sync(FULL, fDL.z.x, 1));
+
+        if (r >= r0) {
+            // F = own forward springs - reactions of the springs that end here
+            Vec2 F = vadd(vadd(vadd(fR, fR2), vadd(fD, fD2)), vadd(fDR, fDL));
+            const Vec2 back = vadd(vadd(vadd(bR, bR2), vadd(fD_1, fD2_2)), vadd(bDR_1, bDL_1));
+            F = vsub(F, back);
+
+            const long long o = (long long)r * p.pitch + cA;
+            unsigned pinw = 0u;
+            if (p.pin_bits && colmem) pinw = __ldg(p.pin_bits + (o >> 5)) >> (o & 31);
+            const bool pinA = pinw & 1u, pinB = (pinw >> 1) & 1u;
+
+            float2 ax = fma2(F.x, bc(p.inv_mass), bc(p.g[0]));
+            float2 ay = fma2(F.y, bc(p.inv_mass), bc(p.g[1]));
+            float2 az = fma2(F.z, bc(p.inv_mass), bc(p.g[2]));
+            if (p.has_wind) {
+                // sin(a + b) = sin(a) cos(b) + cos(a) sin(b), a = base + alpha_r
+                const float2 tr = __ldg(p.wind_rows + r);
+                const float sinR = sinW * tr.y + cosW * tr.x;
+                const float cosR = cosW * tr.y - sinW * tr.x;
+                const float2 w = mul2(bc(p.w_amp), fma2(bc(cosR), sinB, mul2(bc(sinR), cosB)));
+                ax = fma2(w, bc(p.w_dir[0]), ax);
+                ay = fma2(w, bc(p.w_dir[1]), ay);
+                az = fma2(w, bc(p.w_dir[2]), az);
+            }
+            const float2 dt = bc(p.dt);
+            float2 wx = fma2(dt, ax, P0.vx), wy = fma2(dt, ay, P0.vy), wz = fma2(dt, az, P0.vz);
+            float2 xx = fma2(dt, wx, P0.px), xy = fma2(dt, wy, P0.py), xz = fma2(dt, wz, P0.pz);
+            if (pinA) {
+                xx.x = P0.px.x; xy.x = P0.py.x; xz.x = P0.pz.x;
+                wx.x = wy.x = wz.x = 0.0f;
+            }
+            if (pinB) {
+                xx.y = P0.px.y; xy.y = P0.py.y; xz.y = P0.pz.y;
+                wx.y = wy.y = wz.y = 0.0f;
+            }
+            if (MESH) {
+                // nodes whose path box reaches the box of the non-empty grid
+                // cells are marked for the collision phase after the walk
+                const bool needA = okA && !pinA && fmaxf(P0.px.x, xx.x) >= p.mlo[0] &&
+                                   fminf(P0.px.x, xx.x) <= p.mhi[0] && fmaxf(P0.py.x, xy.x) >= p.mlo[1] &&
+                                   fminf(P0.py.x, xy.x) <= p.mhi[1] && fmaxf(P0.pz.x, xz.x) >= p.mlo[2] &&
+                                   fminf(P0.pz.x, xz.x) <= p.mhi[2];
+                const bool needB = okB && !pinB && fmaxf(P0.px.y, xx.y) >= p.mlo[0] &&
+                                   fminf(P0.px.y, xx.y) <= p.mhi[0] && fmaxf(P0.py.y, xy.y) >= p.mlo[1] &&
+                                   fminf(P0.py.y, xy.y) <= p.mhi[1] && fmaxf(P0.pz.y, xz.y) >= p.mlo[2] &&
+                                   fminf(P0.pz.y, xz.y) <= p.mhi[2];
+                markA |= (unsigned long long)needA << (r - r0);
+                markB |= (unsigned long long)needB << (r - r0);
+            }
+            if (okA) {
+                if (!okB) {  // B is padding: keep it zero
+                    xx.y = xy.y = xz.y = wx.y = wy.y = wz.y = 0.0f;
+                }
+                fsum = add2(fsum, add2(add2(add2(xx, xy), add2(xz, wx)), add2(wy, wz)));
+                float *b = out + o;
+                *(float2 *)(b) = xx;
+                *(float2 *)(b + st) = xy;
+                *(float2 *)(b + 2 * st) = xz;
+                *(float2 *)(b + 3 * st) = wx;
+                *(float2 *)(b + 4 * st) = wy;
+                *(float2 *)(b + 5 * st) = wz;
+            }
+        }
+        // shift the window and the carried forces
+        fD2_2 = fD2_1;
+        fD2_1 = fD2;
+        fD_1 = fD;
+        bDR_1 = nDR;
+        bDL_1 = nDL;
+        P0 = P1;
+        P1 = P2;
+        P2 = P3;
+        N0 = N1;
+    }
+
+    if (MESH) {
+        // append the marked nodes to the collision list, row by row so that
+        // consecutive entries are neighbouring columns
+        const unsigned long long mine = markA | markB;
+        const unsigned lo = __reduce_or_sync(FULL, (unsigned)mine);
+        const unsigned hi = __reduce_or_sync(FULL, (unsigned)(mine >> 32));
+        unsigned long long rows = ((unsigned long long)hi << 32) | lo;
+        const int cnt = __popcll(markA) + __popcll(markB);
+        const int total = __reduce_add_sync(FULL, cnt);
+        if (total > 0) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(p.coll_count, (unsigned)total);
+            base = __shfl_sync(FULL, base, 0);
+            while (rows) {
+                const int b = __ffsll((long long)rows) - 1;
+                rows &= rows - 1;
+                const int a = (int)((markA >> b) & 1ull), bb = (int)((markB >> b) & 1ull);
+                int inc = a + bb;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(FULL, inc, d);
+                    if (lane >= d) inc += y;
+                }
+                const int row_total = __shfl_sync(FULL, inc, 31);
+                unsigned w = base + (unsigned)(inc - a - bb);
+                const int o = (r0 + b) * p.pitch + cA;
+                if (a) {
+                    p.coll_list[w] = o;
+                    if (p.coll_cloth) p.coll_cloth[w] = cloth;
+                    w++;
+                }
+                if (bb) {
+                    p.coll_list[w] = o + 1;
+                    if (p.coll_cloth) p.coll_cloth[w] = cloth;
+                }
+                base += (unsigned)row_total;
+            }
+        }
+    }
+}
+
 template <bool MESH, bool PER_SPRING>
 __global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) substep_kernel(const StepParams p)
 {
@@ -183,256 +448,11 @@ __global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) substep_k
     const unsigned long long k = s_k;
     const float *__restrict__ in = (k & 1ull) ? p.state1 : p.state0;
     float *__restrict__ out = (k & 1ull) ? p.state0 : p.state1;
-    const long long st = p.stride;
     const int lane = threadIdx.x & 31;
     const int warp = blockIdx.x * WARPS_PER_CTA + (threadIdx.x >> 5);
     float2 fsum = bc(0.0f);  // sum of every stored value: non-finite iff one of them is
-
-    if (warp < p.strips_x * p.strips_y) {
-        const int sx = warp % p.strips_x, sy = warp / p.strips_x;
-        const int cA = sx * STRIP_COLS - 2 + 2 * lane;  // column of node A (even)
-        const int r0 = sy * p.rows_per_warp;
-        const int r1 = min(r0 + p.rows_per_warp, p.ny);  // output rows [r0, r1)
-        const bool colmem = cA >= 0 && cA < p.pitch;     // both columns addressable
-        const bool out_lane = lane >= 1 && lane <= 30;
-        auto colok = [&](int c) { return c >= 0 && c < p.nx; };
-        // column part of the spring masks (A in .x, B in .y)
-        const float2 mR = make_float2(colok(cA) && colok(cA + 1), colok(cA + 1) && colok(cA + 2));
-        const float2 mR2 = make_float2(colok(cA) && colok(cA + 2), colok(cA + 1) && colok(cA + 3));
-        const float2 mD = make_float2(colok(cA), colok(cA + 1));
-        const float2 mDL = make_float2(colok(cA) && colok(cA - 1), colok(cA + 1) && colok(cA));
-        const bool okA = out_lane && colok(cA), okB = out_lane && colok(cA + 1);
-        // every lane's columns cA-1 .. cA+3 inside the grid
-        const bool colint = sx * STRIP_COLS - 3 >= 0 && sx * STRIP_COLS + 64 < p.nx;
-
-        // wind: sin(alpha_r + beta_c) with beta per column, alpha per row
-        float2 sinB = bc(0.0f), cosB = bc(0.0f);
-        float sinR = 0.0f, cosR = 0.0f, sinK = 0.0f, cosK = 1.0f;
-        if (p.has_wind) {
-            sincosf((float)cA * p.w_kc, &sinB.x, &cosB.x);
-            sincosf((float)(cA + 1) * p.w_kc, &sinB.y, &cosB.y);
-            sincosf(s_wbase + (float)(r0 - 2) * p.w_kr, &sinR, &cosR);  // the walk starts at row r0 - 2
-            sincosf(p.w_kr, &sinK, &cosK);
-        }
-
-        // window: rows r, r+1, r+2 of the walk, starting at r = r0 - 2
-        int r = r0 - 2;
-        Node2 P0 = load_row(in, st, p.pitch, r, p.ny, cA, colmem);
-        Node2 P1 = load_row(in, st, p.pitch, r + 1, p.ny, cA, colmem);
-        Node2 P2 = load_row(in, st, p.pitch, r + 2, p.ny, cA, colmem);
-        Node2 N0 = shfl_down_node(P0);  // lane+1's pair, row r
-        // carried spring forces (owner's forward spring; the reaction is subtracted)
-        Vec2 fD_1 = {}, fD2_1 = {}, fD2_2 = {};  // own down (r-1), down2 (r-1), down2 (r-2)
-        Vec2 bDR_1 = {}, bDL_1 = {};             // reactions of the diagonals of row r-1
-        unsigned long long markA = 0ull, markB = 0ull;  // rows whose node needs the collision phase
-
-        CLOTH_UNROLL(CLOTH_WALK_UNROLL)
-        for (; r < r1; r++) {
-            const Node2 P3 = load_row(in, st, p.pitch, r + 3, p.ny, cA, colmem);  // prefetch
-            const Node2 N1 = shfl_down_node(P1);                                  // lane+1, row r+1
-            Node2 M1;                                                             // lane-1's B, row r+1
-            M1.px.y = __shfl_up_sync(FULL, P1.px.y, 1);
-            M1.py.y = __shfl_up_sync(FULL, P1.py.y, 1);
-            M1.pz.y = __shfl_up_sync(FULL, P1.pz.y, 1);
-            M1.vx.y = __shfl_up_sync(FULL, P1.vx.y, 1);
-            M1.vy.y = __shfl_up_sync(FULL, P1.vy.y, 1);
-            M1.vz.y = __shfl_up_sync(FULL, P1.vz.y, 1);
-
-            // row masks: the spring exists when both ends are grid nodes
-            const float rr0 = (r >= 0 && r < p.ny) ? 1.0f : 0.0f;
-            const float rr1 = (r >= 0 && r + 1 < p.ny) ? 1.0f : 0.0f;
-            const float rr2 = (r >= 0 && r + 2 < p.ny) ? 1.0f : 0.0f;
-
-            float2 ksR, kdR, ksR2, kdR2, ksD, kdD, ksD2, kdD2, ksDR, kdDR, ksDL, kdDL;
-            if (PER_SPRING) {
-                // slot planes hold 0 for springs that do not exist
-                if (r >= 0 && r < p.ny && colmem) {
-                    const long long o = (long long)r * p.pitch + cA;
-                    ksR = __ldg((const float2 *)(p.ks_slot + o));
-                    kdR = __ldg((const float2 *)(p.kd_slot + o));
-                    ksD = __ldg((const float2 *)(p.ks_slot + st + o));
-                    kdD = __ldg((const float2 *)(p.kd_slot + st + o));
-                    ksDR = __ldg((const float2 *)(p.ks_slot + 2 * st + o));
-                    kdDR = __ldg((const float2 *)(p.kd_slot + 2 * st + o));
-                    ksDL = __ldg((const float2 *)(p.ks_slot + 3 * st + o));
-                    kdDL = __ldg((const float2 *)(p.kd_slot + 3 * st + o));
-                    ksR2 = __ldg((const float2 *)(p.ks_slot + 4 * st + o));
-                    kdR2 = __ldg((const float2 *)(p.kd_slot + 4 * st + o));
-                    ksD2 = __ldg((const float2 *)(p.ks_slot + 5 * st + o));
-                    kdD2 = __ldg((const float2 *)(p.kd_slot + 5 * st + o));
-                } else {
-                    ksR = kdR = ksD = kdD = ksDR = kdDR = ksDL = kdDL = ksR2 = kdR2 = ksD2 = kdD2 = bc(0.0f);
-                }
-            } else if (colint && r >= 0 && r + 2 < p.ny) {
-                // interior strip and rows: every spring exists
-                ksR = ksD = bc(p.ks[0]);
-                kdR = kdD = bc(p.kd[0]);
-                ksDR = ksDL = bc(p.ks[1]);
-                kdDR = kdDL = bc(p.kd[1]);
-                ksR2 = ksD2 = bc(p.ks[2]);
-                kdR2 = kdD2 = bc(p.kd[2]);
-            } else {
-                const float2 m0 = mul2(mR, bc(rr0)), m2 = mul2(mR2, bc(rr0));
-                const float2 mD1 = mul2(mD, bc(rr1)), mD2m = mul2(mD, bc(rr2));
-                const float2 mDR1 = mul2(mR, bc(rr1)), mDL1 = mul2(mDL, bc(rr1));
-                ksR = mul2(m0, bc(p.ks[0]));
-                kdR = mul2(m0, bc(p.kd[0]));
-                ksD = mul2(mD1, bc(p.ks[0]));
-                kdD = mul2(mD1, bc(p.kd[0]));
-                ksDR = mul2(mDR1, bc(p.ks[1]));
-                kdDR = mul2(mDR1, bc(p.kd[1]));
-                ksDL = mul2(mDL1, bc(p.ks[1]));
-                kdDL = mul2(mDL1, bc(p.kd[1]));
-                ksR2 = mul2(m2, bc(p.ks[2]));
-                kdR2 = mul2(m2, bc(p.kd[2]));
-                ksD2 = mul2(mD2m, bc(p.ks[2]));
-                kdD2 = mul2(mD2m, bc(p.kd[2]));
-            }
-
-            // the six forward springs of the pair at row r
-            Node2 Q;
-            Q.px = make_float2(P0.px.y, N0.px.x); Q.py = make_float2(P0.py.y, N0.py.x);
-            Q.pz = make_float2(P0.pz.y, N0.pz.x); Q.vx = make_float2(P0.vx.y, N0.vx.x);
-            Q.vy = make_float2(P0.vy.y, N0.vy.x); Q.vz = make_float2(P0.vz.y, N0.vz.x);
-            const Vec2 fR = spring2(P0, Q, ksR, kdR, p.L0[0]);      // (0,+1)
-            const Vec2 fR2 = spring2(P0, N0, ksR2, kdR2, p.L0[4]);  // (0,+2)
-            const Vec2 fD = spring2(P0, P1, ksD, kdD, p.L0[1]);     // (+1,0)
-            const Vec2 fD2 = spring2(P0, P2, ksD2, kdD2, p.L0[5]);  // (+2,0)
-            Q.px = make_float2(P1.px.y, N1.px.x); Q.py = make_float2(P1.py.y, N1.py.x);
-            Q.pz = make_float2(P1.pz.y, N1.pz.x); Q.vx = make_float2(P1.vx.y, N1.vx.x);
-            Q.vy = make_float2(P1.vy.y, N1.vy.x); Q.vz = make_float2(P1.vz.y, N1.vz.x);
-            const Vec2 fDR = spring2(P0, Q, ksDR, kdDR, p.L0[2]);   // (+1,+1)
-            Q.px = make_float2(M1.px.y, P1.px.x); Q.py = make_float2(M1.py.y, P1.py.x);
-            Q.pz = make_float2(M1.pz.y, P1.pz.x); Q.vx = make_float2(M1.vx.y, P1.vx.x);
-            Q.vy = make_float2(M1.vy.y, P1.vy.x); Q.vz = make_float2(M1.vz.y, P1.vz.x);
-            const Vec2 fDL = spring2(P0, Q, ksDL, kdDL, p.L0[3]);   // (+1,-1)
-
-            // reactions arriving at this row from the left neighbours' springs
-            Vec2 bR;  // right spring of (r, c-1): A <- lane-1's B, B <- own A
-            bR.x = make_float2(__shfl_up_sync(FULL, fR.x.y, 1), fR.x.x);
-            bR.y = make_float2(__shfl_up_sync(FULL, fR.y.y, 1), fR.y.x);
-            bR.z = make_float2(__shfl_up_sync(FULL, fR.z.y, 1), fR.z.x);
-            const Vec2 bR2 = {shfl_up2(fR2.x, 1), shfl_up2(fR2.y, 1), shfl_up2(fR2.z, 1)};  // (r, c-2)
-            // diagonals of this row act on row r+1: A <- lane-1's B (down-right),
-            // B <- own A; A <- own B (down-left), B <- lane+1's A
-            Vec2 nDR, nDL;
-            nDR.x = make_float2(__shfl_up_sync(FULL, fDR.x.y, 1), fDR.x.x);
-            nDR.y = make_float2(__shfl_up_sync(FULL, fDR.y.y, 1), fDR.y.x);
-            nDR.z = make_float2(__shfl_up_sync(FULL, fDR.z.y, 1), fDR.z.x);
-            nDL.x = make_float2(fDL.x.y, __shfl_down_sync(FULL, fDL.x.x, 1));
-            nDL.y = make_float2(fDL.y.y, __shfl_down_sync(FULL, fDL.y.x, 1));
-            nDL.z = make_float2(fDL.z.y, __shfl_down_sync(FULL, fDL.z.x, 1));
-
-            if (r >= r0) {
-                // F = own forward springs - reactions of the springs that end here
-                Vec2 F = vadd(vadd(vadd(fR, fR2), vadd(fD, fD2)), vadd(fDR, fDL));
-                const Vec2 back = vadd(vadd(vadd(bR, bR2), vadd(fD_1, fD2_2)), vadd(bDR_1, bDL_1));
-                F = vsub(F, back);
-
-                const long long o = (long long)r * p.pitch + cA;
-                unsigned pinw = 0u;
-                if (p.pin_bits && colmem) pinw = __ldg(p.pin_bits + (o >> 5)) >> (o & 31);
-                const bool pinA = pinw & 1u, pinB = (pinw >> 1) & 1u;
-
-                float2 ax = fma2(F.x, bc(p.inv_mass), bc(p.g[0]));
-                float2 ay = fma2(F.y, bc(p.inv_mass), bc(p.g[1]));
-                float2 az = fma2(F.z, bc(p.inv_mass), bc(p.g[2]));
-                if (p.has_wind) {
-                    // sin(alpha + beta) = sin(alpha) cos(beta) + cos(alpha) sin(beta)
-                    const float2 w = mul2(bc(p.w_amp), fma2(bc(cosR), sinB, mul2(bc(sinR), cosB)));
-                    ax = fma2(w, bc(p.w_dir[0]), ax);
-                    ay = fma2(w, bc(p.w_dir[1]), ay);
-                    az = fma2(w, bc(p.w_dir[2]), az);
-                }
-                const float2 dt = bc(p.dt);
-                float2 wx = fma2(dt, ax, P0.vx), wy = fma2(dt, ay, P0.vy), wz = fma2(dt, az, P0.vz);
-                float2 xx = fma2(dt, wx, P0.px), xy = fma2(dt, wy, P0.py), xz = fma2(dt, wz, P0.pz);
-                if (pinA) {
-                    xx.x = P0.px.x; xy.x = P0.py.x; xz.x = P0.pz.x;
-                    wx.x = wy.x = wz.x = 0.0f;
-                }
-                if (pinB) {
-                    xx.y = P0.px.y; xy.y = P0.py.y; xz.y = P0.pz.y;
-                    wx.y = wy.y = wz.y = 0.0f;
-                }
-                if (MESH) {
-                    // nodes whose path box reaches the box of the non-empty grid
-                    // cells are marked for the collision phase after the walk
-                    const bool needA = okA && !pinA && fmaxf(P0.px.x, xx.x) >= p.mlo[0] &&
-                                       fminf(P0.px.x, xx.x) <= p.mhi[0] && fmaxf(P0.py.x, xy.x) >= p.mlo[1] &&
-                                       fminf(P0.py.x, xy.x) <= p.mhi[1] && fmaxf(P0.pz.x, xz.x) >= p.mlo[2] &&
-                                       fminf(P0.pz.x, xz.x) <= p.mhi[2];
-                    const bool needB = okB && !pinB && fmaxf(P0.px.y, xx.y) >= p.mlo[0] &&
-                                       fminf(P0.px.y, xx.y) <= p.mhi[0] && fmaxf(P0.py.y, xy.y) >= p.mlo[1] &&
-                                       fminf(P0.py.y, xy.y) <= p.mhi[1] && fmaxf(P0.pz.y, xz.y) >= p.mlo[2] &&
-                                       fminf(P0.pz.y, xz.y) <= p.mhi[2];
-                    markA |= (unsigned long long)needA << (r - r0);
-                    markB |= (unsigned long long)needB << (r - r0);
-                }
-                if (okA) {
-                    if (!okB) {  // B is padding: keep it zero
-                        xx.y = xy.y = xz.y = wx.y = wy.y = wz.y = 0.0f;
-                    }
-                    fsum = add2(fsum, add2(add2(add2(xx, xy), add2(xz, wx)), add2(wy, wz)));
-                    float *b = out + o;
-                    *(float2 *)(b) = xx;
-                    *(float2 *)(b + st) = xy;
-                    *(float2 *)(b + 2 * st) = xz;
-                    *(float2 *)(b + 3 * st) = wx;
-                    *(float2 *)(b + 4 * st) = wy;
-                    *(float2 *)(b + 5 * st) = wz;
-                }
-            }
-            if (p.has_wind) {  // advance the row angle by kr
-                const float s2 = sinR * cosK + cosR * sinK;
-                cosR = cosR * cosK - sinR * sinK;
-                sinR = s2;
-            }
-            // shift the window and the carried forces
-            fD2_2 = fD2_1;
-            fD2_1 = fD2;
-            fD_1 = fD;
-            bDR_1 = nDR;
-            bDL_1 = nDL;
-            P0 = P1;
-            P1 = P2;
-            P2 = P3;
-            N0 = N1;
-        }
-
-        if (MESH) {
-            // append the marked nodes to the collision list, row by row so that
-            // consecutive entries are neighbouring columns
-            const unsigned long long mine = markA | markB;
-            const unsigned lo = __reduce_or_sync(FULL, (unsigned)mine);
-            const unsigned hi = __reduce_or_sync(FULL, (unsigned)(mine >> 32));
-            unsigned long long rows = ((unsigned long long)hi << 32) | lo;
-            const int cnt = __popcll(markA) + __popcll(markB);
-            const int total = __reduce_add_sync(FULL, cnt);
-            if (total > 0) {
-                unsigned base = 0;
-                if (lane == 0) base = atomicAdd(p.coll_count, (unsigned)total);
-                base = __shfl_sync(FULL, base, 0);
-                while (rows) {
-                    const int b = __ffsll((long long)rows) - 1;
-                    rows &= rows - 1;
-                    const int a = (int)((markA >> b) & 1ull), bb = (int)((markB >> b) & 1ull);
-                    int inc = a + bb;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const int y = __shfl_up_sync(FULL, inc, d);
-                        if (lane >= d) inc += y;
-                    }
-                    const int row_total = __shfl_sync(FULL, inc, 31);
-                    unsigned w = base + (unsigned)(inc - a - bb);
-                    const int o = (r0 + b) * p.pitch + cA;
-                    if (a) p.coll_list[w++] = o;
-                    if (bb) p.coll_list[w] = o + 1;
-                    base += (unsigned)row_total;
-                }
-            }
-        }
-    }
+    if (warp < p.strips_x * p.strips_y)
+        walk_strip<MESH, PER_SPRING>(p, in, out, s_wbase, warp % p.strips_x, warp / p.strips_x, lane, 0, fsum);
 
     const bool bad = !isfinite(fsum.x + fsum.y);
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
@@ -494,6 +514,107 @@ __global__ void __launch_bounds__(128, 8) collide_kernel(const StepParams p)
             p.ctrl->blocks_done = 0;
             *p.coll_count = 0u;
             p.ctrl->k = k + 1;
+            __threadfence();
+        }
+    }
+}
+
+// ---------------------------------------------------------------- batches
+// Persistent walk over a list of (cloth, strip) items of many cloths: each
+// warp takes the next item from a device counter (items sorted longest
+// first), stages that cloth's parameters in its shared-memory slot and walks
+// the strip with the same code as the single-cloth kernel, so every cloth of a
+// batch gets exactly the arithmetic it gets when stepped alone.
+__global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) batch_substep_kernel(const BatchArgs b)
+{
+    __shared__ StepParams sp[WARPS_PER_CTA];
+    __shared__ unsigned long long s_k;
+    if (threadIdx.x == 0) s_k = *(volatile unsigned long long *)&b.ctrl->k;
+    __syncthreads();
+    const unsigned long long k = s_k;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float2 fsum = bc(0.0f);
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(b.work, 1u);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= b.n_items) break;
+        const int4 it = __ldg(b.items + item);  // (cloth, strip x, strip y, cost)
+        const unsigned *src = (const unsigned *)(b.params + it.x);
+        unsigned *dst = (unsigned *)&sp[wib];
+        for (int w = lane; w < (int)(sizeof(StepParams) / 4); w += 32) dst[w] = __ldg(src + w);
+        __syncwarp();
+        const StepParams &p = sp[wib];
+        const float wbase = p.has_wind ? (float)fmod(p.w_omega * (double)k + p.w_phase0, 6.283185307179586) : 0.0f;
+        const float *in = (k & 1ull) ? p.state1 : p.state0;
+        float *out = (k & 1ull) ? p.state0 : p.state1;
+        if (p.has_mesh) {
+            if (p.ks_slot) walk_strip<true, true>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum);
+            else walk_strip<true, false>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum);
+        } else {
+            if (p.ks_slot) walk_strip<false, true>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum);
+            else walk_strip<false, false>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum);
+        }
+        __syncwarp();  // the slot is rewritten by the next item
+    }
+    if (__any_sync(FULL, !isfinite(fsum.x + fsum.y)) && lane == 0)
+        atomicOr(&b.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // the last CTA re-arms the work counter (the collision kernel advances k)
+        __threadfence();
+        const unsigned prev = atomicAdd(&b.ctrl->blocks_done, 1u);
+        if (prev == gridDim.x - 1) {
+            b.ctrl->blocks_done = 0;
+            *b.work = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// Collision kernel of a batch: every entry carries its cloth index.
+__global__ void __launch_bounds__(128, 8) batch_collide_kernel(const BatchArgs b)
+{
+    __shared__ unsigned long long s_k;
+    __shared__ unsigned s_n;
+    if (threadIdx.x == 0) {
+        s_k = *(volatile unsigned long long *)&b.ctrl->k;
+        s_n = *(volatile unsigned *)b.coll_count;
+    }
+    __syncthreads();
+    const unsigned long long k = s_k;
+    const unsigned n = s_n;
+    float fsum = 0.0f;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int ci = __ldg(b.coll_cloth + i);
+        const long long o = __ldg(b.coll_list + i);
+        const StepParams &p = b.params[ci];
+        const long long st = p.stride;
+        const float *in = (k & 1ull) ? p.state1 : p.state0;
+        float *out = (k & 1ull) ? p.state0 : p.state1;
+        const float sx = __ldg(in + o), sy = __ldg(in + st + o), sz = __ldg(in + 2 * st + o);
+        const float ex = out[o], ey = out[st + o], ez = out[2 * st + o];
+        float ox, oy, oz;
+        if (collide(p, sx, sy, sz, ex, ey, ez, ox, oy, oz)) {
+            out[o] = ox;
+            out[st + o] = oy;
+            out[2 * st + o] = oz;
+            out[3 * st + o] *= p.restitution;
+            out[4 * st + o] *= p.restitution;
+            out[5 * st + o] *= p.restitution;
+            fsum += ox + oy + oz;
+        }
+    }
+    if (__any_sync(FULL, !isfinite(fsum)) && (threadIdx.x & 31) == 0)
+        atomicOr(&b.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&b.ctrl->blocks_done, 1u);
+        if (prev == gridDim.x - 1) {
+            b.ctrl->blocks_done = 0;
+            *b.coll_count = 0u;
+            b.ctrl->k = k + 1;
             __threadfence();
         }
     }
@@ -583,6 +704,19 @@ cudaError_t launch_substep(const StepParams &p, cudaStream_t s)
     }
     return cudaGetLastError();
 }
+
+cudaError_t launch_batch_substep(const BatchArgs &b, cudaStream_t s)
+{
+    batch_substep_kernel<<<b.walk_blocks, 32 * WARPS_PER_CTA, 0, s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_collide_kernel<<<b.coll_blocks, 128, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+int substep_strip_cols() { return STRIP_COLS; }
+int substep_warps_per_cta() { return WARPS_PER_CTA; }
+int substep_min_ctas() { return CLOTH_WALK_MINB; }
 
 cudaError_t launch_aos_to_soa(const float *aos_pos, const float *aos_vel, float *state0, float *state1,
                               long long stride, int n, int nx, int pitch, DevCtrl *ctrl, cudaStream_t s)
