@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-cloth batched leg")
+    ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the e2e leg (default: --steps, max 1000)")
     return ap.parse_args()
 
@@ -225,6 +227,106 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args, stream):
+    """The batched workload: 256 cloths of uneven size (9.3M nodes), each with
+    its own displaced icosphere (1,280-81,920 triangles), 10 substeps per
+    step; one persistent walk + one collision launch per substep (autotuned),
+    against the same cloths stepped by one cloth_step each."""
+    import numpy as np
+    import torch
+
+    import cloth_scenes as cs
+    import paper_2507_11794_gb300 as P
+    scenes = cs.config5()
+    nodes = sum(s.n for s in scenes)
+    sub = scenes[0].substeps
+    b = P.ClothBatch(scenes, stream=int(stream.cuda_stream))
+    tuning = b.tune(10)
+    b.step(2)
+    b.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    b.step(args.batch_steps)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t_batch = ev[0].elapsed_time(ev[1]) / 1e3
+    for i in range(len(scenes)):
+        p, _ = b.read(i)
+        assert np.all(np.isfinite(p))
+    b.close()
+    singles = [P.Cloth(s, stream=int(stream.cuda_stream)) for s in scenes]
+    for c in singles:
+        c.step(1)
+    torch.cuda.synchronize()
+    ks = max(2, args.batch_steps // 4)
+    ev[0].record(stream)
+    for _ in range(ks):
+        for c in singles:
+            c.step(1)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t_single = ev[0].elapsed_time(ev[1]) / 1e3
+    for c in singles:
+        c.close()
+    batch_val = nodes * args.batch_steps / t_batch
+    single_val = nodes * ks / t_single
+    us_sub = 1e6 * t_batch / (args.batch_steps * sub)
+    achieved = BYTES_PER_NODE_SUBSTEP * nodes / (us_sub * 1e-6) / 1e9
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
+    return {"workload": f"256 cloths, sides 16-512 log-uniform (seed 1), {nodes} nodes, each over its own "
+                        f"displaced icosphere (1,280-81,920 triangles); dt=1/1200 s, {sub} substeps per step",
+            "metric": "node-steps/s", "value": batch_val, "steps": args.batch_steps,
+            "ms_per_step": 1e3 * t_batch / args.batch_steps,
+            "per_cloth_launch_value": single_val, "per_cloth_launch_steps": ks,
+            "speedup_vs_per_cloth_launches": batch_val / single_val,
+            "tuning": {"rows_per_warp": tuning.rows_per_warp, "walk_ctas_per_sm": tuning.walk_ctas_per_sm,
+                       "candidates": tuning.candidates},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "scope": "walk + collision launches of one substep",
+                         "algorithmic_bytes_per_substep": BYTES_PER_NODE_SUBSTEP * nodes},
+            "l2": "state (446 MB per substep) larger than L2"}
+
+
+def run_adjoint(stream):
+    """Differentiation workload: 128x128 cloth over a 5,120-triangle icosphere,
+    256-step rollout with checkpoints every 16 steps; times the forward pass
+    and the reverse pass (gradients w.r.t. per-spring ks, kd and v0)."""
+    import torch
+
+    import cloth_scenes as cs
+    import paper_2507_11794_gb300 as P
+    from paper_2507_11794_gb300.rollout import Rollout
+    sc = cs.config4()
+    cl = P.Cloth(sc, stream=int(stream.cuda_stream))
+    ro = Rollout(cl, sc.steps, 16)
+    ks = torch.tensor(sc.ks_spring, device="cuda", requires_grad=True)
+    kd = torch.tensor(sc.kd_spring, device="cuda", requires_grad=True)
+    v0 = torch.tensor(sc.init_vel, device="cuda", requires_grad=True)
+    tgt = torch.tensor(sc.init_pos, device="cuda")
+    fw, bw = [], []
+    for it in range(3):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        pos, _ = ro(ks, kd, v0)
+        ev[1].record(stream)
+        loss = ((pos - tgt) ** 2).sum(1).mean()
+        loss.backward()
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        if it > 0:
+            fw.append(ev[0].elapsed_time(ev[1]))
+            bw.append(ev[1].elapsed_time(ev[2]))
+        ks.grad = kd.grad = v0.grad = None
+    ro.close()
+    cl.close()
+    f, b = min(fw), min(bw)
+    return {"workload": "128x128 cloth (16,384 nodes, 97,026 springs) over a 5,120-triangle icosphere, 256-step "
+                        "rollout, checkpoints every 16 steps, grads w.r.t. per-spring ks, kd and v0",
+            "forward_ms": f, "backward_ms": b, "backward_over_forward": b / f,
+            "forward_node_steps_per_s": sc.n * sc.steps / (f / 1e3)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -289,6 +391,8 @@ def run_ours(args):
     e2e_val = ws * N * ke / e2e_t
 
     cl.close()
+    batch = None if args.no_batch else run_batch(args, stream)
+    adjoint = None if args.no_batch else run_adjoint(stream)
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -304,11 +408,11 @@ def run_ours(args):
                 "avg_launch_us": avg_launch_s * 1e6}
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        rows = 40
-        val, dt, nodes = cpu_oracle_sample(sc, rows, 12)
+        rows, csteps = 400, 30
+        val, dt, nodes = cpu_oracle_sample(sc, rows, csteps)
         cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {rows} rows ({nodes} nodes) of the same cloth with the full mesh, 12 steps x 4 "
-                         f"substeps from the initial state ({dt:.1f} s, FP64, 1 thread)"}
+               "sample": f"first {rows} rows ({nodes} nodes) of the same cloth with the full mesh, {csteps} steps "
+                         f"x 4 substeps from the initial state ({dt:.1f} s, FP64, 1 thread)"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -316,7 +420,7 @@ def run_ours(args):
            "roofline": roofline, "cpu_baseline": cpu,
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 12 * N,
                    "d2h_bytes_per_step": 2 * 12 * N, "steps": ke},
-           "gpu_launches": launches, "clocks": clocks.summary(),
+           "gpu_launches": launches, "clocks": clocks.summary(), "batch": batch, "adjoint": adjoint,
            "wall_s_timed_loop": wall}
     print(json.dumps(out), flush=True)
     if pg is not None:

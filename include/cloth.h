@@ -224,6 +224,39 @@ int cloth_batch_sync(ClothBatch *b);
 /* Release the batch and its cloths.  NULL-safe. */
 void cloth_batch_destroy(ClothBatch *b);
 
+/* ---- differentiation --------------------------------------------------- */
+
+/* A rollout of nsteps steps of one cloth with its reverse pass (not in the
+ * paper): the gradient of a loss on the final state w.r.t. every spring's
+ * stiffness and damping (canonical spring order) and the initial
+ * velocities.  The contact set of every substep is frozen at the one the
+ * forward pass finds (the response is differentiated as a smooth map of the
+ * start point and the path direction).  The forward pass stores the state
+ * every checkpoint_every steps; the backward pass recomputes one segment at
+ * a time, so device memory grows as nsteps/checkpoint_every + checkpoint_every
+ * copies of the state.  All pointers below are device pointers on the
+ * cloth's device; all calls run on the cloth's stream. */
+typedef struct ClothRollout ClothRollout;
+
+/* The cloth's current state (at its current substep count) becomes the
+ * rollout's initial state.  A cloth created without per-spring constants gets
+ * per-spring planes filled from its per-type constants. */
+int cloth_rollout_create(ClothHandle *h, int32_t nsteps, int32_t checkpoint_every, ClothRollout **out);
+/* Forward pass from the initial state: d_ks, d_kd (S floats, canonical
+ * order; NULL keeps the current constants), d_v0 ([N][3] initial velocities;
+ * NULL = the initial state's).  Writes the final state to d_pos_out /
+ * d_vel_out ([N][3], either may be NULL); the cloth then holds that state. */
+int cloth_rollout_forward(ClothRollout *ro, const float *d_ks, const float *d_kd, const float *d_v0, float *d_pos_out,
+                          float *d_vel_out);
+/* Reverse pass of the last forward: d_gpos, d_gvel = dL/d(final positions,
+ * velocities) ([N][3]; d_gvel may be NULL = 0).  Writes dL/dks, dL/dkd (S
+ * floats) and dL/dv0 ([N][3]); any output may be NULL.  The cloth is left in
+ * the final forward state. */
+int cloth_rollout_backward(ClothRollout *ro, const float *d_gpos, const float *d_gvel, float *d_gks, float *d_gkd,
+                           float *d_gv0);
+/* NULL-safe; the cloth itself stays alive. */
+void cloth_rollout_destroy(ClothRollout *ro);
+
 /* ---- allocation-free grid build --------------------------------------- */
 
 /* Largest mesh and grid cloth_grid_build_static accepts. */

@@ -16,6 +16,9 @@ Functions (each cites the passage of the paper it follows, see oracle.c):
                      float32 cell formula; not in the paper, which tests all pairs)
 * ``step``           full substeps: forces, symplectic Euler, collision, the
                      Algorithm 2 response
+* ``adjoint``        reverse mode of ``step`` with the contact set frozen:
+                     gradients w.r.t. final-state adjoints of the initial state and
+                     of per-spring ks, kd (not in the paper)
 """
 from __future__ import annotations
 
@@ -92,6 +95,12 @@ def lib():
             L.oc_step.argtypes = [C.POINTER(OcCloth), C.POINTER(OcMesh), C.POINTER(OcGrid),
                                   dp, dp, C.c_int64, C.c_int32, ip]
             L.oc_step.restype = C.c_int
+            L.oc_step_ex.argtypes = [C.POINTER(OcCloth), C.POINTER(OcMesh), C.POINTER(OcGrid), dp, dp, C.c_int64,
+                                     C.c_int32, ip, dp, dp, dp, C.POINTER(C.c_uint64)]
+            L.oc_step_ex.restype = C.c_int
+            L.oc_adjoint.argtypes = [C.POINTER(OcCloth), C.POINTER(OcMesh), C.POINTER(OcGrid), dp, dp, C.c_int64,
+                                     C.c_int32, dp, dp, dp, dp]
+            L.oc_adjoint.restype = C.c_int
             _lib = L
     return _lib
 
@@ -243,3 +252,41 @@ def run(scene, steps: int, grid: Grid | None = None, x=None, v=None, k0: int = 0
     x = scene.init_pos if x is None else x
     v = scene.init_vel if v is None else v
     return step(cl, x, v, k0, steps * scene.substeps, grid)
+
+
+def step_signature(cloth: Cloth, x, v, k0: int, nsub: int, grid: Grid | None = None):
+    """Like ``step`` (grid broad phase) but also returns a 64-bit signature of
+    every (substep, node, hit triangle, t > delta): equal signatures mean the
+    same contact sets with the same active hits."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1).copy()
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1).copy()
+    sig = C.c_uint64(0xcbf29ce484222325)
+    mesh = C.byref(grid.mesh) if grid is not None else None
+    g = C.byref(grid.g) if grid is not None else None
+    rc = lib().oc_step_ex(C.byref(cloth.c), mesh, g, _ptr(x, C.c_double), _ptr(v, C.c_double), int(k0), int(nsub),
+                          None, None, None, None, C.byref(sig))
+    if rc != 0:
+        raise RuntimeError(f"oc_step_ex failed ({rc})")
+    return x.reshape(-1, 3), v.reshape(-1, 3), sig.value
+
+
+def adjoint(cloth: Cloth, x0, v0, k0: int, nsub: int, lx, lv, grid: Grid | None = None):
+    """Reverse mode of ``nsub`` substeps from (x0, v0): given dL/dx, dL/dv at
+    the end returns (dL/dx0, dL/dv0, dL/dks, dL/dkd), the last two per spring
+    in canonical order (zeros when the cloth has no per-spring arrays is not
+    special: they are the gradients w.r.t. each spring's constants)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
+    v0 = np.ascontiguousarray(v0, dtype=np.float64).reshape(-1)
+    lx = np.ascontiguousarray(lx, dtype=np.float64).reshape(-1).copy()
+    lv = np.ascontiguousarray(lv, dtype=np.float64).reshape(-1).copy()
+    S = lib().oc_springs(cloth.c.nx, cloth.c.ny, None, None, None, 0)
+    gks = np.zeros(S, np.float64)
+    gkd = np.zeros(S, np.float64)
+    mesh = C.byref(grid.mesh) if grid is not None else None
+    g = C.byref(grid.g) if grid is not None else None
+    rc = lib().oc_adjoint(C.byref(cloth.c), mesh, g, _ptr(x0, C.c_double), _ptr(v0, C.c_double), int(k0),
+                          int(nsub), _ptr(lx, C.c_double), _ptr(lv, C.c_double), _ptr(gks, C.c_double),
+                          _ptr(gkd, C.c_double))
+    if rc != 0:
+        raise RuntimeError(f"oc_adjoint failed ({rc})")
+    return lx.reshape(-1, 3), lv.reshape(-1, 3), gks, gkd

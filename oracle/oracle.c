@@ -414,13 +414,83 @@ static void oc_cells_f64(const OcGrid *g, const double S[3], const double E[3], 
 
 /* ------------------------------------------------------------------ step */
 
+/* Candidate triangles of the free node's path S -> E (grid, or all of them
+ * when grid is NULL), into *buf; returns their count. */
+static int64_t oc_candidates(const OcMesh *mesh, const OcGrid *grid, const double S[3], const double E[3],
+                             int32_t **buf, int64_t *bcap)
+{
+    if (grid) {
+        int32_t lo[3], hi[3];
+        oc_cells_f64(grid, S, E, lo, hi);
+        return oc_gather_cells(grid, lo, hi, buf, bcap);
+    }
+    const int64_t nc = mesh->ntris;
+    if (*bcap < nc) {
+        *bcap = nc;
+        *buf = realloc(*buf, sizeof(int32_t) * (size_t)*bcap);
+    }
+    for (int64_t j = 0; j < nc; j++) (*buf)[j] = (int32_t)j;
+    return nc;
+}
+
+/* Hits of the path S -> E (extended MT, candidates in ascending id):
+ * returns K, *acc = sum max(t_k - delta, 0).  With g1/g2 non-NULL also the
+ * sums over the active hits (t_k > delta) of n/a and t n/a, n = e1 x e2,
+ * a = e1.(r x e2): the derivatives dt/dS = n/a and dt/dr = t n/a of the
+ * distance to the triangle's plane along r. */
+static int32_t oc_hits(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, const double S[3],
+                       const double E[3], int32_t **buf, int64_t *bcap, double *acc, double g1[3], double g2[3],
+                       uint64_t *sig)
+{
+    int32_t K = 0;
+    *acc = 0.0;
+    if (g1) g1[0] = g1[1] = g1[2] = g2[0] = g2[1] = g2[2] = 0.0;
+    if (!mesh || mesh->ntris <= 0) return 0;
+    const int64_t nc = oc_candidates(mesh, grid, S, E, buf, bcap);
+    double d[3], L = 0.0, r[3];
+    for (int k = 0; k < 3; k++) { d[k] = E[k] - S[k]; L += d[k] * d[k]; }
+    L = sqrt(L);
+    for (int k = 0; k < 3; k++) r[k] = L > 0.0 ? d[k] / L : 0.0;
+    for (int64_t j = 0; j < nc; j++) {
+        const int32_t tid = (*buf)[j];
+        const int32_t *tr = mesh->tris + 3 * (int64_t)tid;
+        double V[3][3];
+        for (int q = 0; q < 3; q++)
+            for (int k = 0; k < 3; k++) V[q][k] = (double)mesh->verts[3 * (int64_t)tr[q] + k];
+        double th;
+        if (!oc_mt(S, E, V[0], V[1], V[2], cl->eps, cl->t_min, &th)) continue;
+        K++;
+        /* the signature records the hit and which side of the max(t - delta, 0)
+           kink it lies on */
+        if (sig) *sig = (*sig ^ ((uint64_t)(tid + 1) * 2u + (th - cl->delta > 0.0))) * 0x100000001b3ull;
+        if (th - cl->delta > 0.0) {
+            *acc += th - cl->delta;
+            if (g1) {
+                double e1[3], e2[3];
+                for (int k = 0; k < 3; k++) { e1[k] = V[1][k] - V[0][k]; e2[k] = V[2][k] - V[0][k]; }
+                double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                               e1[0] * e2[1] - e1[1] * e2[0]};
+                double a = -(n[0] * r[0] + n[1] * r[1] + n[2] * r[2]);
+                for (int k = 0; k < 3; k++) {
+                    g1[k] += n[k] / a;
+                    g2[k] += th * n[k] / a;
+                }
+            }
+        }
+    }
+    return K;
+}
+
 /* Advance nsub substeps starting at global substep index k0.  x, v: 3N
  * doubles (node-major xyz), updated in place.  mesh may be NULL (no
  * collision).  grid NULL with a mesh means brute force over all triangles.
- * hits (nullable, N ints) receives the hit count K of every node in the last
- * substep.  Returns 0, or -3 on allocation failure. */
-int oc_step(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, double *x, double *v,
-            int64_t k0, int32_t nsub, int32_t *hits)
+ * Optional outputs: hits (N ints) = hit count K of every node in the last
+ * substep; xh, vh, vph (nsub*3N doubles) = position and velocity at the
+ * start of every substep and the velocity after integration; sig = a hash of
+ * every (substep, node, hit triangle) -- equal signatures mean equal contact
+ * sets.  Returns 0, or -3 on allocation failure. */
+int oc_step_ex(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, double *x, double *v, int64_t k0,
+               int32_t nsub, int32_t *hits, double *xh, double *vh, double *vph, uint64_t *sig)
 {
     const int64_t N = (int64_t)cl->nx * cl->ny;
     double *A = malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
@@ -429,12 +499,16 @@ int oc_step(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, double *x
     if (!A) return -3;
     for (int32_t s = 0; s < nsub; s++) {
         double t = (double)(k0 + s) * cl->dt_s;
+        if (xh) memcpy(xh + (int64_t)s * 3 * N, x, sizeof(double) * 3 * (size_t)N);
+        if (vh) memcpy(vh + (int64_t)s * 3 * N, v, sizeof(double) * 3 * (size_t)N);
         oc_accel(cl, x, v, t, A);
         for (int64_t i = 0; i < N; i++) {
             int pinned = cl->pinned && cl->pinned[i];
             if (hits) hits[i] = 0;
             if (pinned) {
                 v[3 * i] = v[3 * i + 1] = v[3 * i + 2] = 0.0;
+                if (vph) vph[((int64_t)s * N + i) * 3] = vph[((int64_t)s * N + i) * 3 + 1] =
+                    vph[((int64_t)s * N + i) * 3 + 2] = 0.0;
                 continue;
             }
             double S[3], E[3];
@@ -442,35 +516,11 @@ int oc_step(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, double *x
                 v[3 * i + k] += cl->dt_s * A[3 * i + k];
                 S[k] = x[3 * i + k];
                 E[k] = S[k] + cl->dt_s * v[3 * i + k];
+                if (vph) vph[((int64_t)s * N + i) * 3 + k] = v[3 * i + k];
             }
-            int32_t K = 0;
-            double acc = 0.0;
-            if (mesh && mesh->ntris > 0) {
-                int64_t nc;
-                if (grid) {
-                    int32_t lo[3], hi[3];
-                    oc_cells_f64(grid, S, E, lo, hi);
-                    nc = oc_gather_cells(grid, lo, hi, &buf, &bcap);
-                } else {
-                    nc = mesh->ntris;
-                    if (bcap < nc) {
-                        bcap = nc;
-                        buf = realloc(buf, sizeof(int32_t) * (size_t)bcap);
-                    }
-                    for (int64_t j = 0; j < nc; j++) buf[j] = (int32_t)j;
-                }
-                for (int64_t j = 0; j < nc; j++) {
-                    const int32_t *tr = mesh->tris + 3 * (int64_t)buf[j];
-                    double V[3][3];
-                    for (int q = 0; q < 3; q++)
-                        for (int k = 0; k < 3; k++) V[q][k] = (double)mesh->verts[3 * (int64_t)tr[q] + k];
-                    double th;
-                    if (oc_mt(S, E, V[0], V[1], V[2], cl->eps, cl->t_min, &th)) {
-                        K++;
-                        acc += th - cl->delta > 0.0 ? th - cl->delta : 0.0;
-                    }
-                }
-            }
+            if (sig) *sig = (*sig ^ (uint64_t)(s * N + i + 1)) * 0x100000001b3ull;
+            double acc;
+            const int32_t K = oc_hits(cl, mesh, grid, S, E, &buf, &bcap, &acc, NULL, NULL, sig);
             if (K > 0) {
                 double L = 0.0, d[3];
                 for (int k = 0; k < 3; k++) { d[k] = E[k] - S[k]; L += d[k] * d[k]; }
@@ -488,5 +538,123 @@ int oc_step(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, double *x
     }
     free(A);
     free(buf);
+    return 0;
+}
+
+int oc_step(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, double *x, double *v, int64_t k0,
+            int32_t nsub, int32_t *hits)
+{
+    return oc_step_ex(cl, mesh, grid, x, v, k0, nsub, hits, NULL, NULL, NULL, NULL);
+}
+
+/* ------------------------------------------------------------- adjoint */
+
+/* Reverse mode of nsub substeps from (x0, v0) at global substep k0, the
+ * contact set of every substep frozen at the one the forward pass finds.
+ * In: lx, lv = dL/dx, dL/dv at the end (3N each); out: the same arrays hold
+ * dL/dx0, dL/dv0, and gks, gkd (S entries, canonical spring order) receive
+ * += dL/dks_s, dL/dkd_s.  Per substep, backwards:
+ *   response  x' = S + m(S, r) r, m = mean over hits of max(t_k - delta, 0),
+ *             r = vs / |vs|, v' = c vs on contact; x' = S + dt vs, v' = vs
+ *             otherwise (pinned: x' = x, v' = 0);
+ *   Euler     vs = v + dt (F(x, v)/m + g + w);
+ *   springs   F as in Algorithm 1, differentiated in x, v, ks, kd.
+ * Returns 0, or -3 on allocation failure. */
+int oc_adjoint(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, const double *x0, const double *v0,
+               int64_t k0, int32_t nsub, double *lx, double *lv, double *gks, double *gkd)
+{
+    const int64_t N = (int64_t)cl->nx * cl->ny;
+    const size_t per = 3 * (size_t)N;
+    double *xh = malloc(sizeof(double) * per * (size_t)nsub);
+    double *vh = malloc(sizeof(double) * per * (size_t)nsub);
+    double *vph = malloc(sizeof(double) * per * (size_t)nsub);
+    double *x = malloc(sizeof(double) * per), *v = malloc(sizeof(double) * per);
+    double *lF = malloc(sizeof(double) * per), *nlx = malloc(sizeof(double) * per), *nlv = malloc(sizeof(double) * per);
+    int32_t *buf = NULL;
+    int64_t bcap = 0;
+    if (!xh || !vh || !vph || !x || !v || !lF || !nlx || !nlv) {
+        free(xh); free(vh); free(vph); free(x); free(v); free(lF); free(nlx); free(nlv);
+        return -3;
+    }
+    memcpy(x, x0, sizeof(double) * per);
+    memcpy(v, v0, sizeof(double) * per);
+    oc_step_ex(cl, mesh, grid, x, v, k0, nsub, NULL, xh, vh, vph, NULL);
+    const double dt = cl->dt_s, c = cl->restitution;
+    for (int32_t s = nsub - 1; s >= 0; s--) {
+        const double *X = xh + (size_t)s * per, *VV = vh + (size_t)s * per, *VP = vph + (size_t)s * per;
+        /* response and integration, node by node */
+        for (int64_t i = 0; i < N; i++) {
+            double *ox = nlx + 3 * i, *ov = nlv + 3 * i, *of = lF + 3 * i;
+            const double *lxi = lx + 3 * i, *lvi = lv + 3 * i;
+            if (cl->pinned && cl->pinned[i]) {
+                for (int k = 0; k < 3; k++) { ox[k] = lxi[k]; ov[k] = 0.0; of[k] = 0.0; }
+                continue;
+            }
+            double S[3], E[3], lvp[3];
+            for (int k = 0; k < 3; k++) { S[k] = X[3 * i + k]; E[k] = S[k] + dt * VP[3 * i + k]; }
+            double acc, g1[3], g2[3];
+            const int32_t K = oc_hits(cl, mesh, grid, S, E, &buf, &bcap, &acc, g1, g2, NULL);
+            if (K > 0) {
+                double nv = sqrt(VP[3 * i] * VP[3 * i] + VP[3 * i + 1] * VP[3 * i + 1] + VP[3 * i + 2] * VP[3 * i + 2]);
+                double r[3], lr[3];
+                for (int k = 0; k < 3; k++) r[k] = VP[3 * i + k] / nv;
+                const double m = acc / (double)K;
+                const double rl = r[0] * lxi[0] + r[1] * lxi[1] + r[2] * lxi[2];
+                for (int k = 0; k < 3; k++) {
+                    ox[k] = lxi[k] + (g1[k] / (double)K) * rl;            /* dx'/dS */
+                    lr[k] = m * lxi[k] + (g2[k] / (double)K) * rl;        /* dx'/dr */
+                }
+                const double rlr = r[0] * lr[0] + r[1] * lr[1] + r[2] * lr[2];
+                for (int k = 0; k < 3; k++) lvp[k] = (lr[k] - r[k] * rlr) / nv + c * lvi[k];
+            } else {
+                for (int k = 0; k < 3; k++) { ox[k] = lxi[k]; lvp[k] = dt * lxi[k] + lvi[k]; }
+            }
+            for (int k = 0; k < 3; k++) { ov[k] = lvp[k]; of[k] = dt / cl->mass * lvp[k]; }
+        }
+        /* springs (Algorithm 1's order), differentiated */
+        int64_t sp = 0;
+        for (int32_t r = 0; r < cl->ny; r++)
+            for (int32_t cc = 0; cc < cl->nx; cc++)
+                for (int d = 0; d < 6; d++) {
+                    int32_t r2 = r + oc_dir_r[d], c2 = cc + oc_dir_c[d];
+                    if (r2 < 0 || r2 >= cl->ny || c2 < 0 || c2 >= cl->nx) continue;
+                    const int32_t a = r * cl->nx + cc, b = r2 * cl->nx + c2;
+                    const int t = oc_dir_t[d];
+                    const double ks = cl->ks_spring ? cl->ks_spring[sp] : cl->ks[t];
+                    const double kd = cl->kd_spring ? cl->kd_spring[sp] : cl->kd[t];
+                    double X1[3], X2[3], L0 = 0.0, dd[3], len = 0.0;
+                    oc_rest(cl, a, X1);
+                    oc_rest(cl, b, X2);
+                    for (int k = 0; k < 3; k++) L0 += (X2[k] - X1[k]) * (X2[k] - X1[k]);
+                    L0 = sqrt(L0);
+                    for (int k = 0; k < 3; k++) { dd[k] = X[3 * b + k] - X[3 * a + k]; len += dd[k] * dd[k]; }
+                    len = sqrt(len);
+                    if (len < 1e-12) { sp++; continue; }
+                    double u[3], dv[3], mu[3], ud = 0.0, um = 0.0;
+                    for (int k = 0; k < 3; k++) {
+                        u[k] = dd[k] / len;
+                        dv[k] = VV[3 * b + k] - VV[3 * a + k];
+                        mu[k] = lF[3 * a + k] - lF[3 * b + k];
+                        ud += u[k] * dv[k];
+                        um += u[k] * mu[k];
+                    }
+                    const double phi = ks * (len - L0) + kd * ud;
+                    if (gks) gks[sp] += um * (len - L0);
+                    if (gkd) gkd[sp] += um * ud;
+                    for (int k = 0; k < 3; k++) {
+                        const double gd = phi / len * (mu[k] - u[k] * um) +
+                                          um * (ks * u[k] + kd / len * (dv[k] - u[k] * ud));
+                        const double gv = kd * u[k] * um;
+                        nlx[3 * b + k] += gd;
+                        nlx[3 * a + k] -= gd;
+                        nlv[3 * b + k] += gv;
+                        nlv[3 * a + k] -= gv;
+                    }
+                    sp++;
+                }
+        memcpy(lx, nlx, sizeof(double) * per);
+        memcpy(lv, nlv, sizeof(double) * per);
+    }
+    free(xh); free(vh); free(vph); free(x); free(v); free(lF); free(nlx); free(nlv); free(buf);
     return 0;
 }

@@ -8,6 +8,8 @@ include/cloth.h); this package is its thin Python face:
 * ``Cloth`` -- a small owner object over one handle, built from a problem
                description (any object with the ClothDesc fields, e.g. a
                ``cloth_scenes.Scene``);
+* ``rollout`` -- differentiable rollouts (torch.autograd.Function over the
+               library's reverse pass);
 * ``build`` -- the in-tree nvcc build.
 
 PyTorch, when present, only supplies the CUDA stream (the current stream of

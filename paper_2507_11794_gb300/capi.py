@@ -36,7 +36,8 @@ EXPORTS = ("cloth_create", "cloth_set_mesh", "cloth_step", "cloth_read", "cloth_
            "cloth_query_candidates", "cloth_grid_build_static",
            "cloth_batch_create", "cloth_batch_set_mesh", "cloth_batch_step", "cloth_batch_read",
            "cloth_batch_set_state", "cloth_batch_tune", "cloth_batch_set_tuning", "cloth_batch_get_tuning",
-           "cloth_batch_sync", "cloth_batch_destroy")
+           "cloth_batch_sync", "cloth_batch_destroy",
+           "cloth_rollout_create", "cloth_rollout_forward", "cloth_rollout_backward", "cloth_rollout_destroy")
 
 
 class ClothError(RuntimeError):
@@ -131,9 +132,15 @@ def lib():
         L.cloth_batch_sync.argtypes = [H]
         L.cloth_batch_destroy.argtypes = [H]
         L.cloth_batch_destroy.restype = None
+        V = C.c_void_p
+        L.cloth_rollout_create.argtypes = [H, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]
+        L.cloth_rollout_forward.argtypes = [H, V, V, V, V, V]
+        L.cloth_rollout_backward.argtypes = [H, V, V, V, V, V]
+        L.cloth_rollout_destroy.argtypes = [H]
+        L.cloth_rollout_destroy.restype = None
         for name in EXPORTS:
             f = getattr(L, name)
-            if name not in ("cloth_destroy", "cloth_last_error", "cloth_batch_destroy"):
+            if name not in ("cloth_destroy", "cloth_last_error", "cloth_batch_destroy", "cloth_rollout_destroy"):
                 f.restype = C.c_int
         _lib = L
         return L
@@ -297,3 +304,26 @@ def cloth_batch_sync(b: int):
 def cloth_batch_destroy(b: int):
     if b:
         lib().cloth_batch_destroy(b)
+
+
+# ---------------------------------------------------------------- rollouts
+
+def cloth_rollout_create(h: int, nsteps: int, checkpoint_every: int) -> int:
+    r = C.c_void_p()
+    check(lib().cloth_rollout_create(h, int(nsteps), int(checkpoint_every), C.byref(r)))
+    return r.value
+
+
+def cloth_rollout_forward(r: int, d_ks: int, d_kd: int, d_v0: int, d_pos: int, d_vel: int):
+    """Device addresses (ints, 0 = NULL)."""
+    check(lib().cloth_rollout_forward(r, d_ks or None, d_kd or None, d_v0 or None, d_pos or None, d_vel or None))
+
+
+def cloth_rollout_backward(r: int, d_gpos: int, d_gvel: int, d_gks: int, d_gkd: int, d_gv0: int):
+    check(lib().cloth_rollout_backward(r, d_gpos or None, d_gvel or None, d_gks or None, d_gkd or None,
+                                       d_gv0 or None))
+
+
+def cloth_rollout_destroy(r: int):
+    if r:
+        lib().cloth_rollout_destroy(r)

@@ -164,7 +164,7 @@ void cloth_fill_params(ClothHandle *h)
     p.ctrl = h->ctrl;
     p.coll_list = h->coll_list;
     p.coll_count = h->ctrl ? &h->ctrl->coll_count : nullptr;
-    p.coll_blocks = h->sm_count * 8;
+    p.coll_blocks = h->sm_count * 2;
 }
 
 namespace {

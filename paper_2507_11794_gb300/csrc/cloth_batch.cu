@@ -118,7 +118,7 @@ cudaError_t rebuild(ClothBatch *b)
     b->args.coll_cloth = b->coll_cloth;
     b->args.coll_count = &b->ctrl->coll_count;
     b->args.walk_blocks = b->sm_count * b->ctas_per_sm;
-    b->args.coll_blocks = b->sm_count * 8;
+    b->args.coll_blocks = b->sm_count * 2;
     return e;
 }
 

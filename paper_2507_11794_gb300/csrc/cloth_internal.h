@@ -55,6 +55,7 @@ struct StepParams {
     float mlo[3], mhi[3];      // box of the grid's non-border cells (early out)
     int *coll_list;            // node offsets marked for the collision kernel (capacity N)
     int *coll_cloth;           // batch mode: cloth index of each entry (nullptr for one cloth)
+    float *vstar;              // optional 3 planes: velocity after integration (adjoint recompute)
     unsigned *coll_count;      // entries in coll_list (reset by the collision kernel)
     int coll_blocks;           // CTAs of the collision kernel
     float delta, eps, tmin, restitution;

@@ -21,6 +21,7 @@
 // every spring is evaluated once, with no atomics and a fixed summation order:
 // results are bitwise reproducible.  The first two rows of each walk only
 // produce the springs that reach into the strip.
+#include "cloth_collide.cuh"
 #include "cloth_internal.h"
 
 namespace {
@@ -106,70 +107,6 @@ __device__ __forceinline__ Vec2 spring2(const Node2 &P, const Node2 &Q, float2 k
     return {mul2(s, ux), mul2(s, uy), mul2(s, uz)};
 }
 
-// Broad + narrow phase and response of one node (scalar).  S = start, E =
-// predicted end; on K > 0 hits returns true and the response position.
-__device__ __forceinline__ bool collide(const StepParams &p, float sx, float sy, float sz, float ex, float ey, float ez,
-                                     float &ox, float &oy, float &oz)
-{
-    const float dx = ex - sx, dy = ey - sy, dz = ez - sz;
-    const float L = sqrtf(dx * dx + dy * dy + dz * dz);
-    if (!(L >= p.eps)) return false;
-    const float rx = dx / L, ry = dy / L, rz = dz / L;
-    const int lox = cell_coord(fminf(sx, ex), p.go[0], p.ginv, p.gd[0]);
-    const int hix = cell_coord(fmaxf(sx, ex), p.go[0], p.ginv, p.gd[0]);
-    const int loy = cell_coord(fminf(sy, ey), p.go[1], p.ginv, p.gd[1]);
-    const int hiy = cell_coord(fmaxf(sy, ey), p.go[1], p.ginv, p.gd[1]);
-    const int loz = cell_coord(fminf(sz, ez), p.go[2], p.ginv, p.gd[2]);
-    const int hiz = cell_coord(fmaxf(sz, ez), p.go[2], p.ginv, p.gd[2]);
-    int K = 0;
-    float acc = 0.0f;
-    for (int cz = loz; cz <= hiz; cz++)
-        for (int cy = loy; cy <= hiy; cy++)
-            for (int cx = lox; cx <= hix; cx++) {
-                const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
-                const int e0 = __ldg(p.cell_start + cell), e1 = __ldg(p.cell_start + cell + 1);
-                for (int e = e0; e < e1; e++) {
-                    const int t = __ldg(p.tri_ids + e);
-                    const float4 A = __ldg(p.tri + 3 * t);
-                    const float4 B = __ldg(p.tri + 3 * t + 1);
-                    const float4 C = __ldg(p.tri + 3 * t + 2);
-                    // a triangle listed in several cells of the box is tested
-                    // only in the first cell the two boxes share
-                    if (max(__float_as_int(A.w), lox) != cx || max(__float_as_int(B.w), loy) != cy ||
-                        max(__float_as_int(C.w), loz) != cz)
-                        continue;
-                    // extended Moller-Trumbore: edge S -> E, direction r, length L
-                    const float hx = ry * C.z - rz * C.y;
-                    const float hy = rz * C.x - rx * C.z;
-                    const float hz = rx * C.y - ry * C.x;
-                    const float a = B.x * hx + B.y * hy + B.z * hz;
-                    if (fabsf(a) < p.eps) continue;
-                    const float f = 1.0f / a;
-                    const float qx0 = sx - A.x, qy0 = sy - A.y, qz0 = sz - A.z;
-                    const float u = f * (qx0 * hx + qy0 * hy + qz0 * hz);
-                    if (u < 0.0f || u > 1.0f) continue;
-                    const float qx = qy0 * B.z - qz0 * B.y;
-                    const float qy = qz0 * B.x - qx0 * B.z;
-                    const float qz = qx0 * B.y - qy0 * B.x;
-                    const float v = f * (rx * qx + ry * qy + rz * qz);
-                    const float th = f * (C.x * qx + C.y * qy + C.z * qz);
-                    if (v < 0.0f || u + v > 1.0f) continue;
-                    if (!(th > p.tmin && th < L)) continue;
-                    K++;
-                    acc += fmaxf(th - p.delta, 0.0f);
-                }
-            }
-    if (K == 0) return false;
-    const float m = acc / (float)K;
-    ox = sx + m * rx;
-    oy = sy + m * ry;
-    oz = sz + m * rz;
-    return true;
-}
-
-// One warp's strip: columns [60 sx - 2, 60 sx + 62) walked down rows
-// [r0 - 2, r0 + rows_per_warp); writes rows [r0, r1) of the output state and,
-// with a surface model, appends the nodes that need the collision kernel.
 template <bool MESH, bool PER_SPRING>
 __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__restrict__ in, float *__restrict__ out,
                                            float wbase, int sx, int sy, int lane, int cloth, float2 &fsum)
@@ -370,6 +307,12 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
                     xx.y = xy.y = xz.y = wx.y = wy.y = wz.y = 0.0f;
                 }
                 fsum = add2(fsum, add2(add2(add2(xx, xy), add2(xz, wx)), add2(wy, wz)));
+                if (p.vstar) {  // velocity after integration, before the response (adjoint recompute)
+                    float *vs = p.vstar + o;
+                    *(float2 *)(vs) = wx;
+                    *(float2 *)(vs + st) = wy;
+                    *(float2 *)(vs + 2 * st) = wz;
+                }
                 float *b = out + o;
                 *(float2 *)(b) = xx;
                 *(float2 *)(b + st) = xy;
