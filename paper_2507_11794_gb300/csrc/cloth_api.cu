@@ -145,6 +145,7 @@ void cloth_fill_params(ClothHandle *h)
     p.tri = h->grid.tri;
     p.cell_start = h->grid.cell_start;
     p.tri_ids = h->grid.tri_ids;
+    p.etri = h->grid.etri;
     for (int a = 0; a < 3; a++) {
         p.go[a] = h->grid.origin[a];
         p.gd[a] = h->grid.dims[a];

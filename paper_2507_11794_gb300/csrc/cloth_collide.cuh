@@ -1,65 +1,114 @@
-// Collision of one node's substep path with the surface model (device code
+// Collision of a node's substep path with the surface model (device code
 // shared by the forward and the reverse pass).
+//
+// Broad phase (Section 4.3): the path S -> E is boxed and the triangles
+// listed in the grid cells of that box are the candidates; a triangle listed
+// in several of those cells is tested only in the first cell the two boxes
+// share.  Narrow phase: the extended Moller-Trumbore test (Algorithm 1) of the
+// path against each candidate.  Response (Algorithm 2): with K hits at
+// distances t_k along r = (E - S)/|E - S|, the node moves to
+// S + mean_k max(t_k - delta, 0) r and its velocity is scaled by the
+// restitution factor.
 #pragma once
 
 #include "cloth_internal.h"
 
-// Broad + narrow phase and response of one node (scalar).  S = start, E =
-// predicted end; on K > 0 hits returns true and the response position.
-// GRAD also returns, for the reverse pass, K, the path length and direction,
-// m = mean max(t_k - delta, 0), and over the active hits (t_k > delta) the
-// sums g1 = sum n/a and g2 = sum t n/a (n = e1 x e2, a = e1.(r x e2)), the
-// derivatives of t_k w.r.t. S and r.  Forward and reverse passes run this one
-// function, so they see the same hits.
+// Path of one node: start S, unit direction r, length L.
+struct CollPath {
+    float sx, sy, sz, rx, ry, rz, L;
+};
+
+// Grid-cell box of a path (cell_coord on both ends, per axis).
+struct CollBox {
+    int lox, loy, loz, hix, hiy, hiz;
+};
+
+__device__ __forceinline__ CollBox coll_box(const StepParams &p, float sx, float sy, float sz, float ex, float ey,
+                                            float ez)
+{
+    CollBox b;
+    b.lox = cell_coord(fminf(sx, ex), p.go[0], p.ginv, p.gd[0]);
+    b.hix = cell_coord(fmaxf(sx, ex), p.go[0], p.ginv, p.gd[0]);
+    b.loy = cell_coord(fminf(sy, ey), p.go[1], p.ginv, p.gd[1]);
+    b.hiy = cell_coord(fmaxf(sy, ey), p.go[1], p.ginv, p.gd[1]);
+    b.loz = cell_coord(fminf(sz, ez), p.go[2], p.ginv, p.gd[2]);
+    b.hiz = cell_coord(fmaxf(sz, ez), p.go[2], p.ginv, p.gd[2]);
+    return b;
+}
+
+// One candidate: grid entry e met in cell (cx, cy, cz) of a box whose low
+// corner is (lox, loy, loz).  Returns true on a hit, with th the distance
+// along r and f = 1/a (a = e1 . (r x e2)); A, B, C receive the triangle
+// record (v0, e1, e2).
+__device__ __forceinline__ bool coll_candidate(const StepParams &p, const CollPath &q, long long e, int cx, int cy,
+                                               int cz, int lox, int loy, int loz, float &th, float &f, float4 &A,
+                                               float4 &B, float4 &C)
+{
+    A = __ldg(p.etri + 3 * e);
+    B = __ldg(p.etri + 3 * e + 1);
+    C = __ldg(p.etri + 3 * e + 2);
+    // the record's w lanes hold the low cell of the triangle's box
+    if (max(__float_as_int(A.w), lox) != cx || max(__float_as_int(B.w), loy) != cy ||
+        max(__float_as_int(C.w), loz) != cz)
+        return false;
+    // extended Moller-Trumbore: edge S -> E, direction r, length L
+    const float hx = q.ry * C.z - q.rz * C.y;
+    const float hy = q.rz * C.x - q.rx * C.z;
+    const float hz = q.rx * C.y - q.ry * C.x;
+    const float a = B.x * hx + B.y * hy + B.z * hz;
+    if (fabsf(a) < p.eps) return false;
+    f = 1.0f / a;
+    const float qx0 = q.sx - A.x, qy0 = q.sy - A.y, qz0 = q.sz - A.z;
+    const float u = f * (qx0 * hx + qy0 * hy + qz0 * hz);
+    if (u < 0.0f || u > 1.0f) return false;
+    const float qx = qy0 * B.z - qz0 * B.y;
+    const float qy = qz0 * B.x - qx0 * B.z;
+    const float qz = qx0 * B.y - qy0 * B.x;
+    const float v = f * (q.rx * qx + q.ry * qy + q.rz * qz);
+    th = f * (C.x * qx + C.y * qy + C.z * qz);
+    if (v < 0.0f || u + v > 1.0f) return false;
+    return th > p.tmin && th < q.L;
+}
+
+// Path of S -> E; false when it is shorter than eps (no test).
+__device__ __forceinline__ bool coll_path(const StepParams &p, float sx, float sy, float sz, float ex, float ey,
+                                          float ez, CollPath &q)
+{
+    const float dx = ex - sx, dy = ey - sy, dz = ez - sz;
+    q.L = sqrtf(dx * dx + dy * dy + dz * dz);
+    if (!(q.L >= p.eps)) return false;
+    q.sx = sx; q.sy = sy; q.sz = sz;
+    q.rx = dx / q.L; q.ry = dy / q.L; q.rz = dz / q.L;
+    return true;
+}
+
+// Broad + narrow phase and response of one node, one thread walking all
+// candidates in (z, y, x) cell order and entry order.  On K > 0 hits returns
+// true and the response position.  GRAD also returns, for the reverse pass,
+// mK = (m, K, r) with m = mean max(t_k - delta, 0), and over the active hits
+// (t_k > delta) the sums g1 = sum n/a and g2 = sum t n/a (n = e1 x e2), the
+// derivatives of t_k w.r.t. S and r.  The cooperative forward kernel below
+// sums the same hits in the same order, so both see the same response.
 template <bool GRAD>
 __device__ __forceinline__ bool collide_t(const StepParams &p, float sx, float sy, float sz, float ex, float ey,
                                           float ez, float &ox, float &oy, float &oz, float *g1 = nullptr,
                                           float *g2 = nullptr, float *mK = nullptr)
 {
-    const float dx = ex - sx, dy = ey - sy, dz = ez - sz;
-    const float L = sqrtf(dx * dx + dy * dy + dz * dz);
-    if (!(L >= p.eps)) return false;
-    const float rx = dx / L, ry = dy / L, rz = dz / L;
-    const int lox = cell_coord(fminf(sx, ex), p.go[0], p.ginv, p.gd[0]);
-    const int hix = cell_coord(fmaxf(sx, ex), p.go[0], p.ginv, p.gd[0]);
-    const int loy = cell_coord(fminf(sy, ey), p.go[1], p.ginv, p.gd[1]);
-    const int hiy = cell_coord(fmaxf(sy, ey), p.go[1], p.ginv, p.gd[1]);
-    const int loz = cell_coord(fminf(sz, ez), p.go[2], p.ginv, p.gd[2]);
-    const int hiz = cell_coord(fmaxf(sz, ez), p.go[2], p.ginv, p.gd[2]);
+    CollPath q;
+    if (!coll_path(p, sx, sy, sz, ex, ey, ez, q)) return false;
+    const CollBox bx = coll_box(p, sx, sy, sz, ex, ey, ez);
     int K = 0;
     float acc = 0.0f;
-    for (int cz = loz; cz <= hiz; cz++)
-        for (int cy = loy; cy <= hiy; cy++)
-            for (int cx = lox; cx <= hix; cx++) {
+    for (int cz = bx.loz; cz <= bx.hiz; cz++)
+        for (int cy = bx.loy; cy <= bx.hiy; cy++)
+            for (int cx = bx.lox; cx <= bx.hix; cx++) {
                 const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
                 const int e0 = __ldg(p.cell_start + cell), e1 = __ldg(p.cell_start + cell + 1);
+#pragma unroll 2
                 for (int e = e0; e < e1; e++) {
-                    const int t = __ldg(p.tri_ids + e);
-                    const float4 A = __ldg(p.tri + 3 * t);
-                    const float4 B = __ldg(p.tri + 3 * t + 1);
-                    const float4 C = __ldg(p.tri + 3 * t + 2);
-                    // a triangle listed in several cells of the box is tested
-                    // only in the first cell the two boxes share
-                    if (max(__float_as_int(A.w), lox) != cx || max(__float_as_int(B.w), loy) != cy ||
-                        max(__float_as_int(C.w), loz) != cz)
-                        continue;
-                    // extended Moller-Trumbore: edge S -> E, direction r, length L
-                    const float hx = ry * C.z - rz * C.y;
-                    const float hy = rz * C.x - rx * C.z;
-                    const float hz = rx * C.y - ry * C.x;
-                    const float a = B.x * hx + B.y * hy + B.z * hz;
-                    if (fabsf(a) < p.eps) continue;
-                    const float f = 1.0f / a;
-                    const float qx0 = sx - A.x, qy0 = sy - A.y, qz0 = sz - A.z;
-                    const float u = f * (qx0 * hx + qy0 * hy + qz0 * hz);
-                    if (u < 0.0f || u > 1.0f) continue;
-                    const float qx = qy0 * B.z - qz0 * B.y;
-                    const float qy = qz0 * B.x - qx0 * B.z;
-                    const float qz = qx0 * B.y - qy0 * B.x;
-                    const float v = f * (rx * qx + ry * qy + rz * qz);
-                    const float th = f * (C.x * qx + C.y * qy + C.z * qz);
-                    if (v < 0.0f || u + v > 1.0f) continue;
-                    if (!(th > p.tmin && th < L)) continue;
+                    float th, f;
+                    float4 A, B, C;
+                    if (!coll_candidate(p, q, e, cx, cy, cz, bx.lox, bx.loy, bx.loz, th, f, A, B, C)) continue;
                     K++;
                     acc += fmaxf(th - p.delta, 0.0f);
                     if (GRAD && th - p.delta > 0.0f) {
@@ -74,20 +123,164 @@ __device__ __forceinline__ bool collide_t(const StepParams &p, float sx, float s
     if (GRAD) {
         mK[0] = m;
         mK[1] = (float)K;
-        mK[2] = rx; mK[3] = ry; mK[4] = rz;
+        mK[2] = q.rx; mK[3] = q.ry; mK[4] = q.rz;
     }
-    ox = sx + m * rx;
-    oy = sy + m * ry;
-    oz = sz + m * rz;
+    ox = sx + m * q.rx;
+    oy = sy + m * q.ry;
+    oz = sz + m * q.rz;
     return true;
 }
 
-// One warp's strip: columns [60 sx - 2, 60 sx + 62) walked down rows
-// [r0 - 2, r0 + rows_per_warp); writes rows [r0, r1) of the output state and,
-// with a surface model, appends the nodes that need the collision kernel.
+// ------------------------------------------------- cooperative list pass
+// The walk appends the nodes whose path box meets the grid's inner cells.
+// Most of them find empty cells; the few next to the surface find about a
+// dozen candidates each, and those sit next to one another in the list.  One
+// thread per node would leave those few threads testing their candidates one
+// after another while the rest of the GPU idles, so each warp instead:
+//  1. takes 32 list entries dealt round robin over all warps (entry i to warp
+//     i mod #warps, spreading a run of neighbouring nodes over many warps),
+//     boxes each path and counts its candidates over the box's cells;
+//  2. spreads the warp's candidates over its 32 lanes, one test per lane and
+//     round; each owner lane then adds its hits in candidate order (the
+//     order collide_t uses, so the sum is the same float sum);
+//  3. owner lanes apply the response.
+// A path whose box spans more than COLL_MAXC cells (a node moving further
+// than a cell in one substep) is handled by its own lane with collide_t.
+constexpr int COLL_WARPS = 4;  // warps per CTA of the collision kernels
+constexpr int COLL_MAXC = 8;   // cells of a box spread over the warp
 
-__device__ __forceinline__ bool collide(const StepParams &p, float sx, float sy, float sz, float ex, float ey, float ez,
-                                        float &ox, float &oy, float &oz)
+struct CollLane {
+    float4 s;                   // S, L
+    float4 r;                   // r, owning cloth (int bits)
+    int4 box;                   // low cell, x extent | y extent << 16
+    int2 cell[COLL_MAXC];       // per cell of the box: first entry, end of the lane's running count
+};
+
+struct CollShared {
+    CollLane lane[COLL_WARPS][32];
+    int base[COLL_WARPS][32];    // first candidate index of each lane (warp exclusive scan)
+    float val[COLL_WARPS][32];   // one round's results: max(t - delta, 0) on a hit, else -1
+};
+
+// Src supplies per list entry i: entry(i, cloth, offset) and params(cloth).
+template <class Src>
+__device__ __forceinline__ void collide_list(const Src &src, CollShared &sh, unsigned long long k, unsigned n,
+                                             float &fsum)
 {
-    return collide_t<false>(p, sx, sy, sz, ex, ey, ez, ox, oy, oz);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned long long nw = (unsigned long long)gridDim.x * COLL_WARPS;
+    const unsigned long long w = (unsigned long long)blockIdx.x * COLL_WARPS + wib;
+    CollLane &me = sh.lane[wib][lane];
+    for (unsigned long long b0 = 0; b0 < n; b0 += 32ull * nw) {
+        const unsigned long long i = b0 + (unsigned long long)lane * nw + w;
+        int cnt = 0, cloth = 0;
+        bool serial = false;
+        long long o = 0;
+        float sx = 0.0f, sy = 0.0f, sz = 0.0f, ex = 0.0f, ey = 0.0f, ez = 0.0f;
+        CollPath q;
+        float *out = nullptr;
+        long long st = 0;
+        if (i < n) {
+            src.entry(i, cloth, o);
+            const StepParams &p = src.params(cloth);
+            st = p.stride;
+            const float *in = (k & 1ull) ? p.state1 : p.state0;
+            out = (k & 1ull) ? p.state0 : p.state1;
+            sx = __ldg(in + o); sy = __ldg(in + st + o); sz = __ldg(in + 2 * st + o);
+            ex = out[o]; ey = out[st + o]; ez = out[2 * st + o];
+            if (coll_path(p, sx, sy, sz, ex, ey, ez, q)) {
+                const CollBox bx = coll_box(p, sx, sy, sz, ex, ey, ez);
+                const int nxc = bx.hix - bx.lox + 1, nyc = bx.hiy - bx.loy + 1, nzc = bx.hiz - bx.loz + 1;
+                if ((long long)nxc * nyc * nzc > COLL_MAXC) {
+                    serial = true;
+                } else {
+                    int c = 0;
+                    for (int cz = bx.loz; cz <= bx.hiz; cz++)
+                        for (int cy = bx.loy; cy <= bx.hiy; cy++)
+                            for (int cx = bx.lox; cx <= bx.hix; cx++, c++) {
+                                const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
+                                const int e0 = __ldg(p.cell_start + cell), e1 = __ldg(p.cell_start + cell + 1);
+                                cnt += e1 - e0;
+                                me.cell[c] = make_int2(e0, cnt);
+                            }
+                    me.s = make_float4(q.sx, q.sy, q.sz, q.L);
+                    me.r = make_float4(q.rx, q.ry, q.rz, __int_as_float(cloth));
+                    me.box = make_int4(bx.lox, bx.loy, bx.loz, nxc | (nyc << 16));
+                }
+            }
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int excl = incl - cnt;
+        sh.base[wib][lane] = excl;
+        __syncwarp();
+        float acc = 0.0f;
+        int K = 0;
+        for (int r0 = 0; r0 < total; r0 += 32) {
+            const int j = r0 + lane;
+            float val = -1.0f;
+            if (j < total) {
+                // owner: the last lane whose first candidate is <= j (it has cnt > 0)
+                int ow = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (sh.base[wib][ow + step] <= j) ow += step;
+                const CollLane &L = sh.lane[wib][ow];
+                const int loc = j - sh.base[wib][ow];
+                int c = 0;
+                while (L.cell[c].y <= loc) c++;
+                const long long e = L.cell[c].x + (loc - (c ? L.cell[c - 1].y : 0));
+                const int nxc = L.box.w & 0xffff, nyc = L.box.w >> 16;
+                const int cx = L.box.x + c % nxc, cy = L.box.y + (c / nxc) % nyc, cz = L.box.z + c / (nxc * nyc);
+                const CollPath lq = {L.s.x, L.s.y, L.s.z, L.r.x, L.r.y, L.r.z, L.s.w};
+                const StepParams &lp = src.params(__float_as_int(L.r.w));
+                float th, f;
+                float4 A, B, C;
+                if (coll_candidate(lp, lq, e, cx, cy, cz, L.box.x, L.box.y, L.box.z, th, f, A, B, C))
+                    val = fmaxf(th - lp.delta, 0.0f);
+            }
+            sh.val[wib][lane] = val;
+            __syncwarp();
+            if (cnt > 0) {
+                const int q0 = max(excl, r0), q1 = min(excl + cnt, r0 + 32);
+                for (int t = q0; t < q1; t++) {
+                    const float v = sh.val[wib][t - r0];
+                    if (v >= 0.0f) {
+                        acc += v;
+                        K++;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (i >= n) continue;
+        const StepParams &p = src.params(cloth);
+        float ox, oy, oz;
+        bool hit;
+        if (serial) {
+            hit = collide_t<false>(p, sx, sy, sz, ex, ey, ez, ox, oy, oz);
+        } else {
+            hit = K > 0;
+            if (hit) {
+                const float m = acc / (float)K;
+                ox = sx + m * q.rx;
+                oy = sy + m * q.ry;
+                oz = sz + m * q.rz;
+            }
+        }
+        if (hit) {
+            out[o] = ox;
+            out[st + o] = oy;
+            out[2 * st + o] = oz;
+            out[3 * st + o] *= p.restitution;
+            out[4 * st + o] *= p.restitution;
+            out[5 * st + o] *= p.restitution;
+            fsum += ox + oy + oz;
+        }
+    }
 }

@@ -186,6 +186,19 @@ __global__ void cell_sort_kernel(const int *__restrict__ cell_start, long long n
     }
 }
 
+// Expand the sorted (cell, triangle) pairs into per-entry records read by the
+// narrow phase without an indirection: the triangle's plane and first cell.
+__global__ void expand_kernel(const float4 *__restrict__ rec, const int *__restrict__ tri_ids, long long n,
+                              float4 *__restrict__ etri)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int t = tri_ids[e];
+    etri[3 * e] = rec[3 * t];
+    etri[3 * e + 1] = rec[3 * t + 1];
+    etri[3 * e + 2] = rec[3 * t + 2];
+}
+
 __global__ void query_kernel(const float4 *__restrict__ rec, const int *__restrict__ cell_start,
                              const int *__restrict__ tri_ids, float ox, float oy, float oz, float inv, int dx, int dy,
                              int dz, const float *__restrict__ S, const float *__restrict__ E, int nseg,
@@ -286,6 +299,7 @@ cudaError_t grid_build(const float *d_verts, const int *d_tris, int nt, DevGrid 
     g->tri = nullptr;
     g->cell_start = nullptr;
     g->tri_ids = nullptr;
+    g->etri = nullptr;
     GTRY(cudaMalloc(&g->tri, sizeof(float4) * 3 * (size_t)nt));
     GTRY(cudaMalloc(&g->cell_start, sizeof(int) * (size_t)(nc + 1)));
     GTRY(cudaMalloc(&box_hi, sizeof(int4) * (size_t)nt));
@@ -321,6 +335,11 @@ cudaError_t grid_build(const float *d_verts, const int *d_tris, int nt, DevGrid 
     GTRY(cudaGetLastError());
     cell_sort_kernel<<<blocks_for(nc, 256), 256, 0, s>>>(g->cell_start, nc, g->tri_ids);
     GTRY(cudaGetLastError());
+    GTRY(cudaMalloc(&g->etri, sizeof(float4) * 3 * (size_t)(htotal > 0 ? htotal : 1)));
+    if (htotal > 0) {
+        expand_kernel<<<blocks_for((long long)htotal, 256), 256, 0, s>>>(g->tri, g->tri_ids, (long long)htotal, g->etri);
+        GTRY(cudaGetLastError());
+    }
     GTRY(cudaStreamSynchronize(s));
 done:
     cudaFree(box_hi);
@@ -337,6 +356,8 @@ void grid_free(DevGrid *g)
     cudaFree(g->tri);
     cudaFree(g->cell_start);
     cudaFree(g->tri_ids);
+    cudaFree(g->etri);
+    g->etri = nullptr;
     g->tri = nullptr;
     g->cell_start = nullptr;
     g->tri_ids = nullptr;

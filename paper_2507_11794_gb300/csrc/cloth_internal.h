@@ -49,6 +49,7 @@ struct StepParams {
     const float4 *tri;         // 3 float4 per triangle: (v0, lo.x) (e1, lo.y) (e2, lo.z)
     const int *cell_start;
     const int *tri_ids;
+    const float4 *etri;        // per grid entry: its triangle's 3 records (no dependent load)
     float go[3];
     float ginv;
     int gd[3];
@@ -94,6 +95,7 @@ struct DevGrid {
     float4 *tri;       // 3 per triangle
     int *cell_start;   // ncells + 1
     int *tri_ids;      // nentries
+    float4 *etri;      // 3 per entry: copy of the entry's triangle record
     int ntris;
 };
 

@@ -416,8 +416,22 @@ __global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) substep_k
 // Second kernel of a substep with a surface model: broad + narrow phase and
 // response of every node the walk marked (one thread per node), then the
 // substep counter advances.
-__global__ void __launch_bounds__(128, 8) collide_kernel(const StepParams p)
+// List entries of one cloth.
+struct OneClothList {
+    const StepParams &p;
+    __device__ void entry(unsigned long long i, int &cloth, long long &o) const
+    {
+        cloth = 0;
+        o = __ldg(p.coll_list + i);
+    }
+    __device__ const StepParams &params(int) const { return p; }
+};
+
+// Collision pass over the nodes the walk listed (cooperative, see
+// collide_list); the last CTA resets the list and advances the substep counter.
+__global__ void __launch_bounds__(32 * COLL_WARPS, 4) collide_kernel(const __grid_constant__ StepParams p)
 {
+    __shared__ CollShared sh;
     __shared__ unsigned long long s_k;
     __shared__ unsigned s_n;
     if (threadIdx.x == 0) {
@@ -426,31 +440,12 @@ __global__ void __launch_bounds__(128, 8) collide_kernel(const StepParams p)
     }
     __syncthreads();
     const unsigned long long k = s_k;
-    const unsigned n = s_n;
-    const float *__restrict__ in = (k & 1ull) ? p.state1 : p.state0;
-    float *out = (k & 1ull) ? p.state0 : p.state1;
-    const long long st = p.stride;
     float fsum = 0.0f;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const long long o = __ldg(p.coll_list + i);
-        const float sx = __ldg(in + o), sy = __ldg(in + st + o), sz = __ldg(in + 2 * st + o);
-        const float ex = out[o], ey = out[st + o], ez = out[2 * st + o];
-        float ox, oy, oz;
-        if (collide(p, sx, sy, sz, ex, ey, ez, ox, oy, oz)) {
-            out[o] = ox;
-            out[st + o] = oy;
-            out[2 * st + o] = oz;
-            out[3 * st + o] *= p.restitution;
-            out[4 * st + o] *= p.restitution;
-            out[5 * st + o] *= p.restitution;
-            fsum += ox + oy + oz;
-        }
-    }
+    collide_list(OneClothList{p}, sh, k, s_n, fsum);
     if (__any_sync(FULL, !isfinite(fsum)) && (threadIdx.x & 31) == 0)
         atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
     __syncthreads();
     if (threadIdx.x == 0) {
-        // the last CTA resets the list and advances the substep counter
         __threadfence();
         const unsigned prev = atomicAdd(&p.ctrl->blocks_done, 1u);
         if (prev == gridDim.x - 1) {
@@ -516,8 +511,20 @@ __global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) batch_sub
 }
 
 // Collision kernel of a batch: every entry carries its cloth index.
-__global__ void __launch_bounds__(128, 8) batch_collide_kernel(const BatchArgs b)
+// List entries of a batch: each carries its cloth.
+struct BatchList {
+    const BatchArgs &b;
+    __device__ void entry(unsigned long long i, int &cloth, long long &o) const
+    {
+        cloth = __ldg(b.coll_cloth + i);
+        o = __ldg(b.coll_list + i);
+    }
+    __device__ const StepParams &params(int c) const { return b.params[c]; }
+};
+
+__global__ void __launch_bounds__(32 * COLL_WARPS, 4) batch_collide_kernel(const __grid_constant__ BatchArgs b)
 {
+    __shared__ CollShared sh;
     __shared__ unsigned long long s_k;
     __shared__ unsigned s_n;
     if (threadIdx.x == 0) {
@@ -526,28 +533,8 @@ __global__ void __launch_bounds__(128, 8) batch_collide_kernel(const BatchArgs b
     }
     __syncthreads();
     const unsigned long long k = s_k;
-    const unsigned n = s_n;
     float fsum = 0.0f;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int ci = __ldg(b.coll_cloth + i);
-        const long long o = __ldg(b.coll_list + i);
-        const StepParams &p = b.params[ci];
-        const long long st = p.stride;
-        const float *in = (k & 1ull) ? p.state1 : p.state0;
-        float *out = (k & 1ull) ? p.state0 : p.state1;
-        const float sx = __ldg(in + o), sy = __ldg(in + st + o), sz = __ldg(in + 2 * st + o);
-        const float ex = out[o], ey = out[st + o], ez = out[2 * st + o];
-        float ox, oy, oz;
-        if (collide(p, sx, sy, sz, ex, ey, ez, ox, oy, oz)) {
-            out[o] = ox;
-            out[st + o] = oy;
-            out[2 * st + o] = oz;
-            out[3 * st + o] *= p.restitution;
-            out[4 * st + o] *= p.restitution;
-            out[5 * st + o] *= p.restitution;
-            fsum += ox + oy + oz;
-        }
-    }
+    collide_list(BatchList{b}, sh, k, s_n, fsum);
     if (__any_sync(FULL, !isfinite(fsum)) && (threadIdx.x & 31) == 0)
         atomicOr(&b.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
     __syncthreads();
@@ -640,7 +627,7 @@ cudaError_t launch_substep(const StepParams &p, cudaStream_t s)
         else substep_kernel<true, false><<<blocks, 32 * WARPS_PER_CTA, 0, s>>>(p);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        collide_kernel<<<p.coll_blocks, 128, 0, s>>>(p);
+        collide_kernel<<<p.coll_blocks, 32 * COLL_WARPS, 0, s>>>(p);
     } else {
         if (per) substep_kernel<false, true><<<blocks, 32 * WARPS_PER_CTA, 0, s>>>(p);
         else substep_kernel<false, false><<<blocks, 32 * WARPS_PER_CTA, 0, s>>>(p);
@@ -653,7 +640,7 @@ cudaError_t launch_batch_substep(const BatchArgs &b, cudaStream_t s)
     batch_substep_kernel<<<b.walk_blocks, 32 * WARPS_PER_CTA, 0, s>>>(b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    batch_collide_kernel<<<b.coll_blocks, 128, 0, s>>>(b);
+    batch_collide_kernel<<<b.coll_blocks, 32 * COLL_WARPS, 0, s>>>(b);
     return cudaGetLastError();
 }
 
