@@ -242,6 +242,9 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
     if (d.nx < 1 || d.ny < 1) return fail(CLOTH_ERR_INVALID_ARG, "nx, ny must be >= 1");
     const long long N = (long long)d.nx * d.ny;
     if (N > (1ll << 30)) return fail(CLOTH_ERR_INVALID_ARG, "too many nodes (%lld)", N);
+    // kernels index a plane with 32-bit offsets r * pitch + c
+    if ((long long)((d.nx + 3) / 4 * 4) * d.ny >= (1ll << 31))
+        return fail(CLOTH_ERR_INVALID_ARG, "plane of %d x %d nodes too large", d.nx, d.ny);
     if (d.substeps < 1) return fail(CLOTH_ERR_INVALID_ARG, "substeps must be >= 1");
     if (!(d.dt > 0.0f) || !isfinite(d.dt)) return fail(CLOTH_ERR_INVALID_ARG, "dt must be finite and > 0");
     if (!(d.total_mass > 0.0f) || !isfinite(d.total_mass))

@@ -21,6 +21,9 @@
 // every spring is evaluated once, with no atomics and a fixed summation order:
 // results are bitwise reproducible.  The first two rows of each walk only
 // produce the springs that reach into the strip.
+#include <type_traits>
+#include <utility>
+
 #include "cloth_collide.cuh"
 #include "cloth_internal.h"
 
@@ -38,6 +41,27 @@ namespace {
 #define CLOTH_UNROLL(n) CLOTH_PRAGMA(unroll n)
 
 constexpr unsigned FULL = 0xffffffffu;
+
+// Programmatic dependent launch: each kernel of a substep lets the next one
+// be launched once all its CTAs are running (launch_dependents), and waits
+// for the previous one to complete, with its writes visible, before it
+// touches any state (wait).  The next kernel's launch and CTA start-up then
+// overlap this kernel's tail instead of following it.
+#ifndef CLOTH_PDL
+#define CLOTH_PDL 1
+#endif
+__device__ __forceinline__ void pdl_wait()
+{
+#if CLOTH_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_launch_dependents()
+{
+#if CLOTH_PDL
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
 constexpr int WARPS_PER_CTA = 4;
 constexpr int STRIP_COLS = 60;
 
@@ -66,25 +90,28 @@ __device__ __forceinline__ float2 shfl_up2(float2 v, int d)
 {
     return make_float2(__shfl_up_sync(FULL, v.x, d), __shfl_up_sync(FULL, v.y, d));
 }
-__device__ __forceinline__ Node2 shfl_down_node(const Node2 &n)
+// Six plane pointers of one state buffer.
+struct Planes {
+    float *k[6];
+};
+__device__ __forceinline__ Planes planes(float *base, long long st)
 {
-    return {shfl_down2(n.px, 1), shfl_down2(n.py, 1), shfl_down2(n.pz, 1),
-            shfl_down2(n.vx, 1), shfl_down2(n.vy, 1), shfl_down2(n.vz, 1)};
+    return {{base, base + st, base + 2 * st, base + 3 * st, base + 4 * st, base + 5 * st}};
 }
 
-// Row r of the lane's two columns (zeros outside the grid's rows / memory).
-__device__ __forceinline__ Node2 load_row(const float *__restrict__ in, long long st, int pitch, int r, int ny, int cA,
-                                          bool colmem)
+// Row r of the lane's two columns (zeros outside the grid's rows / memory);
+// o = r * pitch + cA is a 32-bit plane offset.
+__device__ __forceinline__ Node2 load_row(const Planes &in, int r, int ny, int pitch, int cA, bool colmem)
 {
     Node2 n;
     if (r >= 0 && r < ny && colmem) {
-        const float *b = in + (long long)r * pitch + cA;
-        n.px = __ldg((const float2 *)(b));
-        n.py = __ldg((const float2 *)(b + st));
-        n.pz = __ldg((const float2 *)(b + 2 * st));
-        n.vx = __ldg((const float2 *)(b + 3 * st));
-        n.vy = __ldg((const float2 *)(b + 4 * st));
-        n.vz = __ldg((const float2 *)(b + 5 * st));
+        const unsigned o = (unsigned)r * (unsigned)pitch + (unsigned)cA;
+        n.px = __ldg((const float2 *)(in.k[0] + o));
+        n.py = __ldg((const float2 *)(in.k[1] + o));
+        n.pz = __ldg((const float2 *)(in.k[2] + o));
+        n.vx = __ldg((const float2 *)(in.k[3] + o));
+        n.vy = __ldg((const float2 *)(in.k[4] + o));
+        n.vz = __ldg((const float2 *)(in.k[5] + o));
     } else {
         n.px = n.py = n.pz = n.vx = n.vy = n.vz = make_float2(0.0f, 0.0f);
     }
@@ -92,7 +119,9 @@ __device__ __forceinline__ Node2 load_row(const float *__restrict__ in, long lon
 }
 
 // Hooke's law plus damping along the spring (Algorithm 1) for the pair:
-// d = q - p, F_p = (ks (|d| - L0) + kd (v_q - v_p).d^) d^ (zero for |d|^2 <= 1e-24).
+// d = q - p, F_p = (ks (|d| - L0) + kd (v_q - v_p).d / |d|) d / |d|, written
+// as F_p = s d with s = (ks (|d| - L0) + kd il (v_q - v_p).d) il, il = 1/|d|
+// (zero force for |d|^2 <= 1e-24).
 __device__ __forceinline__ Vec2 spring2(const Node2 &P, const Node2 &Q, float2 ks, float2 kd, float L0)
 {
     const float2 dx = sub2(Q.px, P.px), dy = sub2(Q.py, P.py), dz = sub2(Q.pz, P.pz);
@@ -100,29 +129,37 @@ __device__ __forceinline__ Vec2 spring2(const Node2 &P, const Node2 &Q, float2 k
     float2 il;
     il.x = l2.x > 1e-24f ? rsqrtf(l2.x) : 0.0f;
     il.y = l2.y > 1e-24f ? rsqrtf(l2.y) : 0.0f;
-    const float2 l = mul2(l2, il);
-    const float2 ux = mul2(dx, il), uy = mul2(dy, il), uz = mul2(dz, il);
-    const float2 dvn = fma2(sub2(Q.vz, P.vz), uz, fma2(sub2(Q.vy, P.vy), uy, mul2(sub2(Q.vx, P.vx), ux)));
-    const float2 s = fma2(kd, dvn, mul2(ks, add2(l, bc(-L0))));
-    return {mul2(s, ux), mul2(s, uy), mul2(s, uz)};
+    const float2 dvd = fma2(sub2(Q.vz, P.vz), dz, fma2(sub2(Q.vy, P.vy), dy, mul2(sub2(Q.vx, P.vx), dx)));
+    const float2 e = fma2(l2, il, bc(-L0));  // |d| - L0
+    const float2 sc = mul2(fma2(mul2(kd, il), dvd, mul2(ks, e)), il);
+    return {mul2(sc, dx), mul2(sc, dy), mul2(sc, dz)};
 }
 
+// One warp's strip: columns [60 sx - 2, 60 sx + 62) walked down rows
+// [r0 - 2, r0 + rows_per_warp) with a register window of rows r .. r+2 (row
+// r+3 in flight).  Lane l holds the pair of columns (cA, cA + 1),
+// cA = 60 sx - 2 + 2 l, and evaluates the six springs its two nodes own
+// (Algorithm 1; the forward directions (0,+1), (0,+2), (+1,0), (+2,0),
+// (+1,+1), (+1,-1)); the reaction of each spring reaches the other end
+// through a shuffle (same row) or a register carried to the next row.  Rows
+// r0 - 2 and r0 - 1 are the halo: they evaluate only the springs that end in
+// row r0 or r0 + 1.  Then symplectic Euler with gravity, wind and pins
+// (Section 3) writes rows [r0, r1) of the output state and, with a surface
+// model, the nodes whose path box reaches the grid's inner cells are appended
+// to the collision list.
 template <bool MESH, bool PER_SPRING>
 __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__restrict__ in, float *__restrict__ out,
-                                           float wbase, int sx, int sy, int lane, int cloth, float2 &fsum)
+                                           float wbase, int sx, int sy, int lane, int cloth,
+                                           float2 &fsum)
 {
     const long long st = p.stride;
+    const Planes pin = planes(const_cast<float *>(in), st), pout = planes(out, st);
     const int cA = sx * STRIP_COLS - 2 + 2 * lane;  // column of node A (even)
     const int r0 = sy * p.rows_per_warp;
     const int r1 = min(r0 + p.rows_per_warp, p.ny);  // output rows [r0, r1)
     const bool colmem = cA >= 0 && cA < p.pitch;     // both columns addressable
     const bool out_lane = lane >= 1 && lane <= 30;
     auto colok = [&](int c) { return c >= 0 && c < p.nx; };
-    // column part of the spring masks (A in .x, B in .y)
-    const float2 mR = make_float2(colok(cA) && colok(cA + 1), colok(cA + 1) && colok(cA + 2));
-    const float2 mR2 = make_float2(colok(cA) && colok(cA + 2), colok(cA + 1) && colok(cA + 3));
-    const float2 mD = make_float2(colok(cA), colok(cA + 1));
-    const float2 mDL = make_float2(colok(cA) && colok(cA - 1), colok(cA + 1) && colok(cA));
     const bool okA = out_lane && colok(cA), okB = out_lane && colok(cA + 1);
     // every lane's columns cA-1 .. cA+3 inside the grid
     const bool colint = sx * STRIP_COLS - 3 >= 0 && sx * STRIP_COLS + 64 < p.nx;
@@ -144,54 +181,72 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
         }
         sincosf(wbase, &sinW, &cosW);
     }
+    // per-row inputs, fetched one row ahead: the row's wind table entry and pin bits
+    auto row_inputs = [&](int r, float2 &tr, unsigned &pinw) {
+        tr = make_float2(0.0f, 1.0f);
+        pinw = 0u;
+        if (r < r1) {
+            if (p.has_wind) tr = __ldg(p.wind_rows + r);
+            if (p.pin_bits && colmem) {
+                const unsigned o = (unsigned)r * (unsigned)p.pitch + (unsigned)cA;
+                pinw = __ldg(p.pin_bits + (o >> 5)) >> (o & 31u);
+            }
+        }
+    };
+    float2 trN;
+    unsigned pinN;
+    row_inputs(r0, trN, pinN);
 
-    // window: rows r, r+1, r+2 of the walk, starting at r = r0 - 2
     int r = r0 - 2;
-    Node2 P0 = load_row(in, st, p.pitch, r, p.ny, cA, colmem);
-    Node2 P1 = load_row(in, st, p.pitch, r + 1, p.ny, cA, colmem);
-    Node2 P2 = load_row(in, st, p.pitch, r + 2, p.ny, cA, colmem);
-    Node2 N0 = shfl_down_node(P0);  // lane+1's pair, row r
+    Node2 P0 = load_row(pin, r, p.ny, p.pitch, cA, colmem);
+    Node2 P1 = load_row(pin, r + 1, p.ny, p.pitch, cA, colmem);
+    Node2 P2 = load_row(pin, r + 2, p.ny, p.pitch, cA, colmem);
+    Node2 N0{};  // lane+1's pair, row r (from row r0 on)
     // carried spring forces (owner's forward spring; the reaction is subtracted)
     Vec2 fD_1 = {}, fD2_1 = {}, fD2_2 = {};  // own down (r-1), down2 (r-1), down2 (r-2)
     Vec2 bDR_1 = {}, bDL_1 = {};             // reactions of the diagonals of row r-1
     unsigned long long markA = 0ull, markB = 0ull;  // rows whose node needs the collision phase
 
-    CLOTH_UNROLL(CLOTH_WALK_UNROLL)
-    for (; r < r1; r++) {
-        const Node2 P3 = load_row(in, st, p.pitch, r + 3, p.ny, cA, colmem);  // prefetch
-        const Node2 N1 = shfl_down_node(P1);                                  // lane+1, row r+1
-        Node2 M1;                                                             // lane-1's B, row r+1
-        M1.px.y = __shfl_up_sync(FULL, P1.px.y, 1);
-        M1.py.y = __shfl_up_sync(FULL, P1.py.y, 1);
-        M1.pz.y = __shfl_up_sync(FULL, P1.pz.y, 1);
-        M1.vx.y = __shfl_up_sync(FULL, P1.vx.y, 1);
-        M1.vy.y = __shfl_up_sync(FULL, P1.vy.y, 1);
-        M1.vz.y = __shfl_up_sync(FULL, P1.vz.y, 1);
-
-        // row masks: the spring exists when both ends are grid nodes
-        const float rr0 = (r >= 0 && r < p.ny) ? 1.0f : 0.0f;
-        const float rr1 = (r >= 0 && r + 1 < p.ny) ? 1.0f : 0.0f;
-        const float rr2 = (r >= 0 && r + 2 < p.ny) ? 1.0f : 0.0f;
+    // PH 0: row r0-2 (only its (+2,0) spring reaches an output row);
+    // PH 1: row r0-1 (its (+1,*) and (+2,0) springs); PH 2: output rows
+    auto row = [&](auto phase) {
+        constexpr int PH = decltype(phase)::value;
+        const Node2 P3 = load_row(pin, r + 3, p.ny, p.pitch, cA, colmem);  // prefetch
+        Node2 N1{}, M1{};  // lane+1's pair and lane-1's B, row r+1
+        if (PH >= 1) {
+            N1.px = shfl_down2(P1.px, 1); N1.py = shfl_down2(P1.py, 1); N1.pz = shfl_down2(P1.pz, 1);
+            N1.vx = shfl_down2(P1.vx, 1); N1.vy = shfl_down2(P1.vy, 1); N1.vz = shfl_down2(P1.vz, 1);
+            M1.px.y = __shfl_up_sync(FULL, P1.px.y, 1);
+            M1.py.y = __shfl_up_sync(FULL, P1.py.y, 1);
+            M1.pz.y = __shfl_up_sync(FULL, P1.pz.y, 1);
+            M1.vx.y = __shfl_up_sync(FULL, P1.vx.y, 1);
+            M1.vy.y = __shfl_up_sync(FULL, P1.vy.y, 1);
+            M1.vz.y = __shfl_up_sync(FULL, P1.vz.y, 1);
+        }
 
         float2 ksR, kdR, ksR2, kdR2, ksD, kdD, ksD2, kdD2, ksDR, kdDR, ksDL, kdDL;
         if (PER_SPRING) {
             // slot planes hold 0 for springs that do not exist
+            ksR = kdR = ksD = kdD = ksDR = kdDR = ksDL = kdDL = ksR2 = kdR2 = ksD2 = kdD2 = bc(0.0f);
             if (r >= 0 && r < p.ny && colmem) {
-                const long long o = (long long)r * p.pitch + cA;
-                ksR = __ldg((const float2 *)(p.ks_slot + o));
-                kdR = __ldg((const float2 *)(p.kd_slot + o));
-                ksD = __ldg((const float2 *)(p.ks_slot + st + o));
-                kdD = __ldg((const float2 *)(p.kd_slot + st + o));
-                ksDR = __ldg((const float2 *)(p.ks_slot + 2 * st + o));
-                kdDR = __ldg((const float2 *)(p.kd_slot + 2 * st + o));
-                ksDL = __ldg((const float2 *)(p.ks_slot + 3 * st + o));
-                kdDL = __ldg((const float2 *)(p.kd_slot + 3 * st + o));
-                ksR2 = __ldg((const float2 *)(p.ks_slot + 4 * st + o));
-                kdR2 = __ldg((const float2 *)(p.kd_slot + 4 * st + o));
-                ksD2 = __ldg((const float2 *)(p.ks_slot + 5 * st + o));
-                kdD2 = __ldg((const float2 *)(p.kd_slot + 5 * st + o));
-            } else {
-                ksR = kdR = ksD = kdD = ksDR = kdDR = ksDL = kdDL = ksR2 = kdR2 = ksD2 = kdD2 = bc(0.0f);
+                const unsigned o = (unsigned)r * (unsigned)p.pitch + (unsigned)cA;
+                const float *ks = p.ks_slot + o, *kd = p.kd_slot + o;
+                ksD2 = __ldg((const float2 *)(ks + 5 * st));
+                kdD2 = __ldg((const float2 *)(kd + 5 * st));
+                if (PH >= 1) {
+                    ksD = __ldg((const float2 *)(ks + st));
+                    kdD = __ldg((const float2 *)(kd + st));
+                    ksDR = __ldg((const float2 *)(ks + 2 * st));
+                    kdDR = __ldg((const float2 *)(kd + 2 * st));
+                    ksDL = __ldg((const float2 *)(ks + 3 * st));
+                    kdDL = __ldg((const float2 *)(kd + 3 * st));
+                }
+                if (PH == 2) {
+                    ksR = __ldg((const float2 *)(ks));
+                    kdR = __ldg((const float2 *)(kd));
+                    ksR2 = __ldg((const float2 *)(ks + 4 * st));
+                    kdR2 = __ldg((const float2 *)(kd + 4 * st));
+                }
             }
         } else if (colint && r >= 0 && r + 2 < p.ny) {
             // interior strip and rows: every spring exists
@@ -202,6 +257,14 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
             ksR2 = ksD2 = bc(p.ks[2]);
             kdR2 = kdD2 = bc(p.kd[2]);
         } else {
+            // a spring exists when both ends are grid nodes (A in .x, B in .y)
+            const float2 mR = make_float2(colok(cA) && colok(cA + 1), colok(cA + 1) && colok(cA + 2));
+            const float2 mR2 = make_float2(colok(cA) && colok(cA + 2), colok(cA + 1) && colok(cA + 3));
+            const float2 mD = make_float2(colok(cA), colok(cA + 1));
+            const float2 mDL = make_float2(colok(cA) && colok(cA - 1), colok(cA + 1) && colok(cA));
+            const float rr0 = (r >= 0 && r < p.ny) ? 1.0f : 0.0f;
+            const float rr1 = (r >= 0 && r + 1 < p.ny) ? 1.0f : 0.0f;
+            const float rr2 = (r >= 0 && r + 2 < p.ny) ? 1.0f : 0.0f;
             const float2 m0 = mul2(mR, bc(rr0)), m2 = mul2(mR2, bc(rr0));
             const float2 mD1 = mul2(mD, bc(rr1)), mD2m = mul2(mD, bc(rr2));
             const float2 mDR1 = mul2(mR, bc(rr1)), mDL1 = mul2(mDL, bc(rr1));
@@ -219,49 +282,55 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
             kdD2 = mul2(mD2m, bc(p.kd[2]));
         }
 
-        // the six forward springs of the pair at row r
-        Node2 Q;
-        Q.px = make_float2(P0.px.y, N0.px.x); Q.py = make_float2(P0.py.y, N0.py.x);
-        Q.pz = make_float2(P0.pz.y, N0.pz.x); Q.vx = make_float2(P0.vx.y, N0.vx.x);
-        Q.vy = make_float2(P0.vy.y, N0.vy.x); Q.vz = make_float2(P0.vz.y, N0.vz.x);
-        const Vec2 fR = spring2(P0, Q, ksR, kdR, p.L0[0]);      // (0,+1)
-        const Vec2 fR2 = spring2(P0, N0, ksR2, kdR2, p.L0[4]);  // (0,+2)
-        const Vec2 fD = spring2(P0, P1, ksD, kdD, p.L0[1]);     // (+1,0)
+        // the forward springs of the pair at row r
         const Vec2 fD2 = spring2(P0, P2, ksD2, kdD2, p.L0[5]);  // (+2,0)
-        Q.px = make_float2(P1.px.y, N1.px.x); Q.py = make_float2(P1.py.y, N1.py.x);
-        Q.pz = make_float2(P1.pz.y, N1.pz.x); Q.vx = make_float2(P1.vx.y, N1.vx.x);
-        Q.vy = make_float2(P1.vy.y, N1.vy.x); Q.vz = make_float2(P1.vz.y, N1.vz.x);
-        const Vec2 fDR = spring2(P0, Q, ksDR, kdDR, p.L0[2]);   // (+1,+1)
-        Q.px = make_float2(M1.px.y, P1.px.x); Q.py = make_float2(M1.py.y, P1.py.x);
-        Q.pz = make_float2(M1.pz.y, P1.pz.x); Q.vx = make_float2(M1.vx.y, P1.vx.x);
-        Q.vy = make_float2(M1.vy.y, P1.vy.x); Q.vz = make_float2(M1.vz.y, P1.vz.x);
-        const Vec2 fDL = spring2(P0, Q, ksDL, kdDL, p.L0[3]);   // (+1,-1)
-
-        // reactions arriving at this row from the left neighbours' springs
-        Vec2 bR;  // right spring of (r, c-1): A <- lane-1's B, B <- own A
-        bR.x = make_float2(__shfl_up_sync(FULL, fR.x.y, 1), fR.x.x);
-        bR.y = make_float2(__shfl_up_sync(FULL, fR.y.y, 1), fR.y.x);
-        bR.z = make_float2(__shfl_up_sync(FULL, fR.z.y, 1), fR.z.x);
-        const Vec2 bR2 = {shfl_up2(fR2.x, 1), shfl_up2(fR2.y, 1), shfl_up2(fR2.z, 1)};  // (r, c-2)
+        Vec2 fD{}, fDR{}, fDL{}, fR{}, fR2{};
+        Node2 Q;
+        if (PH >= 1) {
+            fD = spring2(P0, P1, ksD, kdD, p.L0[1]);  // (+1,0)
+            Q.px = make_float2(P1.px.y, N1.px.x); Q.py = make_float2(P1.py.y, N1.py.x);
+            Q.pz = make_float2(P1.pz.y, N1.pz.x); Q.vx = make_float2(P1.vx.y, N1.vx.x);
+            Q.vy = make_float2(P1.vy.y, N1.vy.x); Q.vz = make_float2(P1.vz.y, N1.vz.x);
+            fDR = spring2(P0, Q, ksDR, kdDR, p.L0[2]);  // (+1,+1)
+            Q.px = make_float2(M1.px.y, P1.px.x); Q.py = make_float2(M1.py.y, P1.py.x);
+            Q.pz = make_float2(M1.pz.y, P1.pz.x); Q.vx = make_float2(M1.vx.y, P1.vx.x);
+            Q.vy = make_float2(M1.vy.y, P1.vy.x); Q.vz = make_float2(M1.vz.y, P1.vz.x);
+            fDL = spring2(P0, Q, ksDL, kdDL, p.L0[3]);  // (+1,-1)
+        }
+        if (PH == 2) {
+            Q.px = make_float2(P0.px.y, N0.px.x); Q.py = make_float2(P0.py.y, N0.py.x);
+            Q.pz = make_float2(P0.pz.y, N0.pz.x); Q.vx = make_float2(P0.vx.y, N0.vx.x);
+            Q.vy = make_float2(P0.vy.y, N0.vy.x); Q.vz = make_float2(P0.vz.y, N0.vz.x);
+            fR = spring2(P0, Q, ksR, kdR, p.L0[0]);      // (0,+1)
+            fR2 = spring2(P0, N0, ksR2, kdR2, p.L0[4]);  // (0,+2)
+        }
         // diagonals of this row act on row r+1: A <- lane-1's B (down-right),
         // B <- own A; A <- own B (down-left), B <- lane+1's A
-        Vec2 nDR, nDL;
-        nDR.x = make_float2(__shfl_up_sync(FULL, fDR.x.y, 1), fDR.x.x);
-        nDR.y = make_float2(__shfl_up_sync(FULL, fDR.y.y, 1), fDR.y.x);
-        nDR.z = make_float2(__shfl_up_sync(FULL, fDR.z.y, 1), fDR.z.x);
-        nDL.x = make_float2(fDL.x.y, __shfl_down_sync(FULL, fDL.x.x, 1));
-        nDL.y = make_float2(fDL.y.y, __shfl_down_sync(FULL, fDL.y.x, 1));
-        nDL.z = make_float2(fDL.z.y, __shfl_down_sync(FULL, fDL.z.x, 1));
+        Vec2 nDR{}, nDL{};
+        if (PH >= 1) {
+            nDR.x = make_float2(__shfl_up_sync(FULL, fDR.x.y, 1), fDR.x.x);
+            nDR.y = make_float2(__shfl_up_sync(FULL, fDR.y.y, 1), fDR.y.x);
+            nDR.z = make_float2(__shfl_up_sync(FULL, fDR.z.y, 1), fDR.z.x);
+            nDL.x = make_float2(fDL.x.y, __shfl_down_sync(FULL, fDL.x.x, 1));
+            nDL.y = make_float2(fDL.y.y, __shfl_down_sync(FULL, fDL.y.x, 1));
+            nDL.z = make_float2(fDL.z.y, __shfl_down_sync(FULL, fDL.z.x, 1));
+        }
 
-        if (r >= r0) {
+        if (PH == 2) {
+            const float2 tr = trN;
+            const unsigned pinw = pinN;
+            row_inputs(r + 1, trN, pinN);
+            // reactions arriving at this row from the left neighbours' springs
+            Vec2 bR;  // right spring of (r, c-1): A <- lane-1's B, B <- own A
+            bR.x = make_float2(__shfl_up_sync(FULL, fR.x.y, 1), fR.x.x);
+            bR.y = make_float2(__shfl_up_sync(FULL, fR.y.y, 1), fR.y.x);
+            bR.z = make_float2(__shfl_up_sync(FULL, fR.z.y, 1), fR.z.x);
+            const Vec2 bR2 = {shfl_up2(fR2.x, 1), shfl_up2(fR2.y, 1), shfl_up2(fR2.z, 1)};  // (r, c-2)
+
             // F = own forward springs - reactions of the springs that end here
             Vec2 F = vadd(vadd(vadd(fR, fR2), vadd(fD, fD2)), vadd(fDR, fDL));
             const Vec2 back = vadd(vadd(vadd(bR, bR2), vadd(fD_1, fD2_2)), vadd(bDR_1, bDL_1));
             F = vsub(F, back);
-
-            const long long o = (long long)r * p.pitch + cA;
-            unsigned pinw = 0u;
-            if (p.pin_bits && colmem) pinw = __ldg(p.pin_bits + (o >> 5)) >> (o & 31);
             const bool pinA = pinw & 1u, pinB = (pinw >> 1) & 1u;
 
             float2 ax = fma2(F.x, bc(p.inv_mass), bc(p.g[0]));
@@ -269,7 +338,6 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
             float2 az = fma2(F.z, bc(p.inv_mass), bc(p.g[2]));
             if (p.has_wind) {
                 // sin(a + b) = sin(a) cos(b) + cos(a) sin(b), a = base + alpha_r
-                const float2 tr = __ldg(p.wind_rows + r);
                 const float sinR = sinW * tr.y + cosW * tr.x;
                 const float cosR = cosW * tr.y - sinW * tr.x;
                 const float2 w = mul2(bc(p.w_amp), fma2(bc(cosR), sinB, mul2(bc(sinR), cosB)));
@@ -307,19 +375,19 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
                     xx.y = xy.y = xz.y = wx.y = wy.y = wz.y = 0.0f;
                 }
                 fsum = add2(fsum, add2(add2(add2(xx, xy), add2(xz, wx)), add2(wy, wz)));
+                const unsigned o = (unsigned)r * (unsigned)p.pitch + (unsigned)cA;
                 if (p.vstar) {  // velocity after integration, before the response (adjoint recompute)
                     float *vs = p.vstar + o;
                     *(float2 *)(vs) = wx;
                     *(float2 *)(vs + st) = wy;
                     *(float2 *)(vs + 2 * st) = wz;
                 }
-                float *b = out + o;
-                *(float2 *)(b) = xx;
-                *(float2 *)(b + st) = xy;
-                *(float2 *)(b + 2 * st) = xz;
-                *(float2 *)(b + 3 * st) = wx;
-                *(float2 *)(b + 4 * st) = wy;
-                *(float2 *)(b + 5 * st) = wz;
+                *(float2 *)(pout.k[0] + o) = xx;
+                *(float2 *)(pout.k[1] + o) = xy;
+                *(float2 *)(pout.k[2] + o) = xz;
+                *(float2 *)(pout.k[3] + o) = wx;
+                *(float2 *)(pout.k[4] + o) = wy;
+                *(float2 *)(pout.k[5] + o) = wz;
             }
         }
         // shift the window and the carried forces
@@ -332,7 +400,12 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
         P1 = P2;
         P2 = P3;
         N0 = N1;
-    }
+        r++;
+    };
+    row(std::integral_constant<int, 0>());
+    row(std::integral_constant<int, 1>());
+    CLOTH_UNROLL(CLOTH_WALK_UNROLL)
+    while (r < r1) row(std::integral_constant<int, 2>());
 
     if (MESH) {
         // append the marked nodes to the collision list, row by row so that
@@ -380,6 +453,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) substep_k
 {
     __shared__ unsigned long long s_k;
     __shared__ float s_wbase;
+    pdl_launch_dependents();
+    pdl_wait();
     if (threadIdx.x == 0) {
         const unsigned long long k = *(volatile unsigned long long *)&p.ctrl->k;
         s_k = k;
@@ -395,7 +470,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) substep_k
     const int warp = blockIdx.x * WARPS_PER_CTA + (threadIdx.x >> 5);
     float2 fsum = bc(0.0f);  // sum of every stored value: non-finite iff one of them is
     if (warp < p.strips_x * p.strips_y)
-        walk_strip<MESH, PER_SPRING>(p, in, out, s_wbase, warp % p.strips_x, warp / p.strips_x, lane, 0, fsum);
+        walk_strip<MESH, PER_SPRING>(p, in, out, s_wbase, warp % p.strips_x,
+                                     warp / p.strips_x, lane, 0, fsum);
 
     const bool bad = !isfinite(fsum.x + fsum.y);
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
@@ -434,6 +510,8 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, 4) collide_kernel(const __gri
     __shared__ CollShared sh;
     __shared__ unsigned long long s_k;
     __shared__ unsigned s_n;
+    pdl_launch_dependents();
+    pdl_wait();
     if (threadIdx.x == 0) {
         s_k = *(volatile unsigned long long *)&p.ctrl->k;
         s_n = *(volatile unsigned *)p.coll_count;
@@ -467,6 +545,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) batch_sub
 {
     __shared__ StepParams sp[WARPS_PER_CTA];
     __shared__ unsigned long long s_k;
+    pdl_launch_dependents();
+    pdl_wait();
     if (threadIdx.x == 0) s_k = *(volatile unsigned long long *)&b.ctrl->k;
     __syncthreads();
     const unsigned long long k = s_k;
@@ -527,6 +607,8 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, 4) batch_collide_kernel(const
     __shared__ CollShared sh;
     __shared__ unsigned long long s_k;
     __shared__ unsigned s_n;
+    pdl_launch_dependents();
+    pdl_wait();
     if (threadIdx.x == 0) {
         s_k = *(volatile unsigned long long *)&b.ctrl->k;
         s_n = *(volatile unsigned *)b.coll_count;
@@ -617,31 +699,49 @@ void substep_shape(StepParams &p)
     p.strips_y = (p.ny + p.rows_per_warp - 1) / p.rows_per_warp;
 }
 
+namespace {
+// Kernel launch with the programmatic-serialisation attribute (see pdl_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), int blocks, int threads, cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = CLOTH_PDL;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+}  // namespace
+
 cudaError_t launch_substep(const StepParams &p, cudaStream_t s)
 {
     const int warps = p.strips_x * p.strips_y;
     const int blocks = (warps + WARPS_PER_CTA - 1) / WARPS_PER_CTA;
     const bool per = p.ks_slot != nullptr;
+    const int threads = 32 * WARPS_PER_CTA;
+    cudaError_t e;
     if (p.has_mesh) {
-        if (per) substep_kernel<true, true><<<blocks, 32 * WARPS_PER_CTA, 0, s>>>(p);
-        else substep_kernel<true, false><<<blocks, 32 * WARPS_PER_CTA, 0, s>>>(p);
-        cudaError_t e = cudaGetLastError();
+        e = per ? launch_k(substep_kernel<true, true>, blocks, threads, s, p)
+                : launch_k(substep_kernel<true, false>, blocks, threads, s, p);
         if (e != cudaSuccess) return e;
-        collide_kernel<<<p.coll_blocks, 32 * COLL_WARPS, 0, s>>>(p);
+        e = launch_k(collide_kernel, p.coll_blocks, 32 * COLL_WARPS, s, p);
     } else {
-        if (per) substep_kernel<false, true><<<blocks, 32 * WARPS_PER_CTA, 0, s>>>(p);
-        else substep_kernel<false, false><<<blocks, 32 * WARPS_PER_CTA, 0, s>>>(p);
+        e = per ? launch_k(substep_kernel<false, true>, blocks, threads, s, p)
+                : launch_k(substep_kernel<false, false>, blocks, threads, s, p);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_batch_substep(const BatchArgs &b, cudaStream_t s)
 {
-    batch_substep_kernel<<<b.walk_blocks, 32 * WARPS_PER_CTA, 0, s>>>(b);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_k(batch_substep_kernel, b.walk_blocks, 32 * WARPS_PER_CTA, s, b);
     if (e != cudaSuccess) return e;
-    batch_collide_kernel<<<b.coll_blocks, 32 * COLL_WARPS, 0, s>>>(b);
-    return cudaGetLastError();
+    return launch_k(batch_collide_kernel, b.coll_blocks, 32 * COLL_WARPS, s, b);
 }
 
 int substep_strip_cols() { return STRIP_COLS; }
