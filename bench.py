@@ -371,8 +371,17 @@ def run_ours(args):
     assert np.all(np.isfinite(pos)) and np.all(np.isfinite(vel))
     t = max_over_ranks(pg, dev_ms / 1e3)
     value = ws * N * args.steps / t
-    launches = SUB * args.steps
-    avg_launch_s = (dev_ms / 1e3) / launches
+    launches = 2 * SUB * args.steps  # walk + collision kernel per substep
+
+    # per-kernel durations: the same steps (L2 flushed before each), every
+    # kernel launch bracketed by CUDA events on the library's stream
+    prof_steps = min(args.steps, 200)
+    walk_us = coll_us = 0.0
+    for i in range(prof_steps):
+        flush.fill_(float(i))
+        w, c = cl.profile_substeps(SUB)
+        walk_us += w / prof_steps
+        coll_us += c / prof_steps
 
     # end to end through the C ABI: pinned host state in, step, state out
     ke = args.e2e_steps or min(args.steps, 1000)
@@ -401,11 +410,14 @@ def run_ours(args):
     peaks = measured_peaks()
     peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
     peak_src = "measured" if peaks and "hbm_gbs" in peaks else "fallback"
-    achieved = BYTES_PER_NODE_SUBSTEP * N / avg_launch_s / 1e9
+    achieved = BYTES_PER_NODE_SUBSTEP * N / (walk_us * 1e-6) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profile_traffic(), "peak_source": peak_src,
-                "kernel": "substep_kernel<MESH=true>", "algorithmic_bytes_per_launch": BYTES_PER_NODE_SUBSTEP * N,
-                "avg_launch_us": avg_launch_s * 1e6}
+                "kernel": "substep_kernel<MESH=true> (walk: springs + integration)",
+                "algorithmic_bytes_per_launch": BYTES_PER_NODE_SUBSTEP * N,
+                "avg_launch_us": walk_us, "collide_kernel_avg_launch_us": coll_us,
+                "timing": f"CUDA events around each launch, {prof_steps} steps x {SUB} substeps after the timed "
+                          f"region, L2 flushed before each step"}
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         rows, csteps = 400, 30

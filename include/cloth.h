@@ -181,6 +181,17 @@ int cloth_get_grid(ClothHandle *h, int32_t *cell_start, int32_t *tri_ids);
 int cloth_query_candidates(ClothHandle *h, const float *S, const float *E, int32_t nseg,
                            int32_t *counts, int32_t *ids, int32_t cap);
 
+/* Advance nsub substeps with every kernel launch bracketed by CUDA events
+ * (captured into a graph and replayed once on the handle's stream, so the
+ * launches run back to back), and report the mean device
+ * duration per launch in microseconds: walk_us for the force + integration
+ * kernel (Algorithm 1 and Section 3), collide_us for the collision kernel
+ * (Section 4.3 and Algorithm 2; 0 without a surface model).  The state
+ * advances exactly as with cloth_step.  nsub in [1, 4096]; either output may
+ * be NULL.  Synchronises.  Errors: CLOTH_ERR_INVALID_ARG, CLOTH_ERR_CUDA,
+ * and the flag errors of cloth_sync. */
+int cloth_profile_substeps(ClothHandle *h, int32_t nsub, float *walk_us, float *collide_us);
+
 /* ---- batches of cloths ------------------------------------------------- */
 
 /* Many independent cloths (each with its own grid, constants, pins and

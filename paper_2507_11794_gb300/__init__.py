@@ -115,6 +115,10 @@ class Cloth:
     def info(self):
         return capi.cloth_get_info(self.h)
 
+    def profile_substeps(self, nsub: int):
+        """(walk_us, collide_us): mean device time per launch of each kernel."""
+        return capi.cloth_profile_substeps(self.h, nsub)
+
     def grid(self):
         return capi.cloth_get_grid(self.h)
 

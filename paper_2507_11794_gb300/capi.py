@@ -33,7 +33,7 @@ _NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5
 # Every symbol include/cloth.h declares (checked by the CPU test-suite).
 EXPORTS = ("cloth_create", "cloth_set_mesh", "cloth_step", "cloth_read", "cloth_destroy",
            "cloth_set_state", "cloth_sync", "cloth_last_error", "cloth_get_info", "cloth_get_grid",
-           "cloth_query_candidates", "cloth_grid_build_static",
+           "cloth_query_candidates", "cloth_grid_build_static", "cloth_profile_substeps",
            "cloth_batch_create", "cloth_batch_set_mesh", "cloth_batch_step", "cloth_batch_read",
            "cloth_batch_set_state", "cloth_batch_tune", "cloth_batch_set_tuning", "cloth_batch_get_tuning",
            "cloth_batch_sync", "cloth_batch_destroy",
@@ -212,6 +212,14 @@ def cloth_get_info(h: int) -> ClothInfo:
     info = ClothInfo()
     check(lib().cloth_get_info(h, C.byref(info)))
     return info
+
+
+def cloth_profile_substeps(h: int, nsub: int):
+    """Mean device microseconds per launch of the walk and collision kernels
+    over nsub substeps (the state advances)."""
+    w, c = C.c_float(), C.c_float()
+    check(lib().cloth_profile_substeps(h, int(nsub), C.byref(w), C.byref(c)))
+    return float(w.value), float(c.value)
 
 
 def cloth_get_grid(h: int):

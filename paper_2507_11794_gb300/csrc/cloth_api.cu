@@ -485,6 +485,58 @@ int cloth_set_state(ClothHandle *h, const float *pos, const float *vel)
     return CLOTH_OK;
 }
 
+int cloth_profile_substeps(ClothHandle *h, int32_t nsub, float *walk_us, float *collide_us)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (nsub < 1 || nsub > 4096) return fail(CLOTH_ERR_INVALID_ARG, "nsub must be in [1, 4096]");
+    DeviceScope ds(h->device);
+    const int ne = 3 * nsub;
+    std::vector<cudaEvent_t> ev(ne, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < ne && e == cudaSuccess; i++) e = cudaEventCreate(&ev[i]);
+    // captured into a graph, so the GPU runs the launches back to back
+    // instead of waiting for the host between them
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = cudaSuccess;
+        for (int i = 0; i < nsub && le == cudaSuccess; i++) {
+            le = cudaEventRecord(ev[3 * i], h->cap_stream);
+            if (le == cudaSuccess) le = launch_walk(h->params, h->cap_stream);
+            if (le == cudaSuccess) le = cudaEventRecord(ev[3 * i + 1], h->cap_stream);
+            if (le == cudaSuccess && h->has_mesh) le = launch_collide(h->params, h->cap_stream);
+            if (le == cudaSuccess) le = cudaEventRecord(ev[3 * i + 2], h->cap_stream);
+        }
+        e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    double tw = 0.0, tc = 0.0;
+    for (int i = 0; i < nsub && e == cudaSuccess; i++) {
+        float a = 0.0f, b = 0.0f;
+        e = cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]);
+        tw += a;
+        tc += b;
+    }
+    for (int i = 0; i < ne; i++)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "profiled substeps");
+    h->substeps_done += nsub;
+    if (walk_us) *walk_us = (float)(1e3 * tw / nsub);
+    if (collide_us) *collide_us = h->has_mesh ? (float)(1e3 * tc / nsub) : 0.0f;
+    unsigned flags = 0;
+    rc = read_flags(h, &flags);
+    if (rc) return rc;
+    return flags_status(flags);
+}
+
 int cloth_sync(ClothHandle *h)
 {
     int rc = check_handle(h);

@@ -65,6 +65,10 @@ struct StepParams {
 
 // Launch one substep (reads state k&1, writes the other, advances ctrl->k).
 cudaError_t launch_substep(const StepParams &p, cudaStream_t s);
+// The two kernels of a substep separately (with a surface model, the walk
+// leaves the counter to the collision kernel).
+cudaError_t launch_walk(const StepParams &p, cudaStream_t s);
+cudaError_t launch_collide(const StepParams &p, cudaStream_t s);
 
 // A batch of cloths stepped by one persistent walk launch per substep.
 struct BatchArgs {

@@ -718,22 +718,28 @@ cudaError_t launch_k(void (*kern)(KArgs...), int blocks, int threads, cudaStream
 }
 }  // namespace
 
-cudaError_t launch_substep(const StepParams &p, cudaStream_t s)
+cudaError_t launch_walk(const StepParams &p, cudaStream_t s)
 {
     const int warps = p.strips_x * p.strips_y;
     const int blocks = (warps + WARPS_PER_CTA - 1) / WARPS_PER_CTA;
     const bool per = p.ks_slot != nullptr;
     const int threads = 32 * WARPS_PER_CTA;
-    cudaError_t e;
-    if (p.has_mesh) {
-        e = per ? launch_k(substep_kernel<true, true>, blocks, threads, s, p)
-                : launch_k(substep_kernel<true, false>, blocks, threads, s, p);
-        if (e != cudaSuccess) return e;
-        e = launch_k(collide_kernel, p.coll_blocks, 32 * COLL_WARPS, s, p);
-    } else {
-        e = per ? launch_k(substep_kernel<false, true>, blocks, threads, s, p)
-                : launch_k(substep_kernel<false, false>, blocks, threads, s, p);
-    }
+    if (p.has_mesh)
+        return per ? launch_k(substep_kernel<true, true>, blocks, threads, s, p)
+                   : launch_k(substep_kernel<true, false>, blocks, threads, s, p);
+    return per ? launch_k(substep_kernel<false, true>, blocks, threads, s, p)
+               : launch_k(substep_kernel<false, false>, blocks, threads, s, p);
+}
+
+cudaError_t launch_collide(const StepParams &p, cudaStream_t s)
+{
+    return launch_k(collide_kernel, p.coll_blocks, 32 * COLL_WARPS, s, p);
+}
+
+cudaError_t launch_substep(const StepParams &p, cudaStream_t s)
+{
+    cudaError_t e = launch_walk(p, s);
+    if (e == cudaSuccess && p.has_mesh) e = launch_collide(p, s);
     return e;
 }
 
