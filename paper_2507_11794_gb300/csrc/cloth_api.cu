@@ -165,7 +165,7 @@ void cloth_fill_params(ClothHandle *h)
     p.ctrl = h->ctrl;
     p.coll_list = h->coll_list;
     p.coll_count = h->ctrl ? &h->ctrl->coll_count : nullptr;
-    p.coll_blocks = h->sm_count * 2;
+    p.coll_blocks = h->sm_count * CLOTH_COLL_CTAS_PER_SM;
 }
 
 namespace {
@@ -502,12 +502,14 @@ int cloth_profile_substeps(ClothHandle *h, int32_t nsub, float *walk_us, float *
     if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t le = cudaSuccess;
+        // external records: timestamp nodes in the graph, not capture-internal joins
+        auto rec = [&](cudaEvent_t x) { return cudaEventRecordWithFlags(x, h->cap_stream, cudaEventRecordExternal); };
         for (int i = 0; i < nsub && le == cudaSuccess; i++) {
-            le = cudaEventRecord(ev[3 * i], h->cap_stream);
+            le = rec(ev[3 * i]);
             if (le == cudaSuccess) le = launch_walk(h->params, h->cap_stream);
-            if (le == cudaSuccess) le = cudaEventRecord(ev[3 * i + 1], h->cap_stream);
+            if (le == cudaSuccess) le = rec(ev[3 * i + 1]);
             if (le == cudaSuccess && h->has_mesh) le = launch_collide(h->params, h->cap_stream);
-            if (le == cudaSuccess) le = cudaEventRecord(ev[3 * i + 2], h->cap_stream);
+            if (le == cudaSuccess) le = rec(ev[3 * i + 2]);
         }
         e = cudaStreamEndCapture(h->cap_stream, &g);
         if (le != cudaSuccess) e = le;

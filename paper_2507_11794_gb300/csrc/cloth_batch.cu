@@ -118,7 +118,7 @@ cudaError_t rebuild(ClothBatch *b)
     b->args.coll_cloth = b->coll_cloth;
     b->args.coll_count = &b->ctrl->coll_count;
     b->args.walk_blocks = b->sm_count * b->ctas_per_sm;
-    b->args.coll_blocks = b->sm_count * 2;
+    b->args.coll_blocks = b->sm_count * CLOTH_COLL_CTAS_PER_SM;
     return e;
 }
 

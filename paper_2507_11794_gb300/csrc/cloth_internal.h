@@ -63,6 +63,11 @@ struct StepParams {
     DevCtrl *ctrl;
 };
 
+// CTAs per SM of the collision kernels (grid = SMs x this).
+#ifndef CLOTH_COLL_CTAS_PER_SM
+#define CLOTH_COLL_CTAS_PER_SM 4
+#endif
+
 // Launch one substep (reads state k&1, writes the other, advances ctrl->k).
 cudaError_t launch_substep(const StepParams &p, cudaStream_t s);
 // The two kernels of a substep separately (with a surface model, the walk

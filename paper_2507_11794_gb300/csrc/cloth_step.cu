@@ -37,6 +37,9 @@ namespace {
 #ifndef CLOTH_WALK_UNROLL
 #define CLOTH_WALK_UNROLL 1
 #endif
+#ifndef CLOTH_COLL_MINB
+#define CLOTH_COLL_MINB 4
+#endif
 #define CLOTH_PRAGMA(x) _Pragma(#x)
 #define CLOTH_UNROLL(n) CLOTH_PRAGMA(unroll n)
 
@@ -505,7 +508,7 @@ struct OneClothList {
 
 // Collision pass over the nodes the walk listed (cooperative, see
 // collide_list); the last CTA resets the list and advances the substep counter.
-__global__ void __launch_bounds__(32 * COLL_WARPS, 4) collide_kernel(const __grid_constant__ StepParams p)
+__global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kernel(const __grid_constant__ StepParams p)
 {
     __shared__ CollShared sh;
     __shared__ unsigned long long s_k;
@@ -602,7 +605,7 @@ struct BatchList {
     __device__ const StepParams &params(int c) const { return b.params[c]; }
 };
 
-__global__ void __launch_bounds__(32 * COLL_WARPS, 4) batch_collide_kernel(const __grid_constant__ BatchArgs b)
+__global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) batch_collide_kernel(const __grid_constant__ BatchArgs b)
 {
     __shared__ CollShared sh;
     __shared__ unsigned long long s_k;
