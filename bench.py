@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the 256-cloth batched leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched, adjoint and atomic A/B legs")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the e2e leg (default: --steps, max 1000)")
     return ap.parse_args()
@@ -327,6 +327,45 @@ def run_adjoint(stream):
             "forward_node_steps_per_s": sc.n * sc.steps / (f / 1e3)}
 
 
+def run_atomic_ab(stream, flush, steps: int = 100):
+    """The paper's force pass (Algorithm 1: one thread per spring, FP32
+    atomic adds, then a per-node integration kernel) against the fused column
+    walk, on the benchmark workload: the first `steps` steps from the initial
+    state, L2 flushed before each, per-step CUDA events; then per-kernel
+    times over 20 more steps."""
+    import torch
+
+    import cloth_scenes as cs
+    import paper_2507_11794_gb300 as P
+    sc = cs.config3("l6")
+    out = {"workload": f"the benchmark workload, first {steps} steps from the initial state, L2 flushed per step"}
+    for name, flags in (("fused_walk", 0), ("atomic_springs", P.capi.CLOTH_FLAG_ATOMIC_SPRINGS)):
+        cl = P.Cloth(sc, stream=int(stream.cuda_stream), flags=flags)
+        for _ in range(3):
+            cl.step(1)
+        cl.set_state(sc.init_pos, sc.init_vel)
+        cl.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            cl.step(1)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        w = c = 0.0
+        for i in range(20):
+            flush.fill_(float(i))
+            wi, ci = cl.profile_substeps(sc.substeps)
+            w += wi / 20
+            c += ci / 20
+        cl.close()
+        out[name] = {"node_steps_per_s": sc.n * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                     "force_integrate_us_per_substep": w, "collide_us_per_substep": c}
+    out["fused_over_atomic"] = out["fused_walk"]["node_steps_per_s"] / out["atomic_springs"]["node_steps_per_s"]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -402,6 +441,7 @@ def run_ours(args):
     cl.close()
     batch = None if args.no_batch else run_batch(args, stream)
     adjoint = None if args.no_batch else run_adjoint(stream)
+    atomic_ab = None if args.no_batch else run_atomic_ab(stream, flush)
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -432,7 +472,7 @@ def run_ours(args):
            "roofline": roofline, "cpu_baseline": cpu,
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 12 * N,
                    "d2h_bytes_per_step": 2 * 12 * N, "steps": ke},
-           "gpu_launches": launches, "clocks": clocks.summary(), "batch": batch, "adjoint": adjoint,
+           "gpu_launches": launches, "clocks": clocks.summary(), "batch": batch, "adjoint": adjoint, "atomic_springs_ab": atomic_ab,
            "wall_s_timed_loop": wall}
     print(json.dumps(out), flush=True)
     if pg is not None:

@@ -58,6 +58,15 @@ enum {
 
 /* Flags of ClothDesc.flags */
 #define CLOTH_FLAG_NO_GRAPH 1u /* launch substeps one by one instead of a CUDA graph */
+/* Evaluate the spring forces as Algorithm 1 prints them: one thread per
+ * spring adding F to one end and -F to the other with FP32 atomic adds into a
+ * per-node force buffer (16 B per node, zeroed again by the integration kernel
+ * as Algorithm 2 resets its buffers), then one thread per node integrating.
+ * The force law, integrator and collision phase are those of the default
+ * path, but the order of the additions, and so the last bits of the state,
+ * vary from run to run.  Kept as an A/B of the paper's design against the
+ * default fused column walk.  Not accepted by cloth_batch_create. */
+#define CLOTH_FLAG_ATOMIC_SPRINGS 2u
 
 /* Sinusoidal external acceleration field (N/kg) added to gravity:
  *   w(X0, t) = amp * dir * sin(2*pi*freq*t + kappa*(udir . X0) + phase),

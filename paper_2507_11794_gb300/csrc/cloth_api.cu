@@ -80,6 +80,8 @@ void free_all(ClothHandle *h)
     h->coll_list = nullptr;
     cudaFree(h->wind_tab);
     h->wind_tab = nullptr;
+    cudaFree(h->force);
+    h->force = nullptr;
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->state = nullptr;
     h->pin_bits = nullptr;
@@ -163,6 +165,7 @@ void cloth_fill_params(ClothHandle *h)
     p.tmin = d.mt_t_min;
     p.restitution = d.restitution;
     p.ctrl = h->ctrl;
+    p.force = h->force;
     p.coll_list = h->coll_list;
     p.coll_count = h->ctrl ? &h->ctrl->coll_count : nullptr;
     p.coll_blocks = h->sm_count * CLOTH_COLL_CTAS_PER_SM;
@@ -326,6 +329,11 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
                 if ((e = upload(h->pin_bits, bits.data(), sizeof(uint32_t) * bits.size(), h->stream)) != cudaSuccess)
                     break;
             }
+        }
+        if (d.flags & CLOTH_FLAG_ATOMIC_SPRINGS) {
+            const size_t nf = (size_t)h->pitch * d.ny;
+            if ((e = cudaMalloc(&h->force, sizeof(float4) * nf)) != cudaSuccess) break;
+            if ((e = cudaMemsetAsync(h->force, 0, sizeof(float4) * nf, h->stream)) != cudaSuccess) break;
         }
         if (d.wind.amp != 0.0f) {
             // (sin, cos) of kappa*(udir.dv)*row and kappa*(udir.du)*col, in double

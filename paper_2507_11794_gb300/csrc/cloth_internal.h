@@ -57,6 +57,7 @@ struct StepParams {
     int *coll_list;            // node offsets marked for the collision kernel (capacity N)
     int *coll_cloth;           // batch mode: cloth index of each entry (nullptr for one cloth)
     float *vstar;              // optional 3 planes: velocity after integration (adjoint recompute)
+    float4 *force;             // per-node force buffer of the atomic spring path, or nullptr
     unsigned *coll_count;      // entries in coll_list (reset by the collision kernel)
     int coll_blocks;           // CTAs of the collision kernel
     float delta, eps, tmin, restitution;
@@ -71,8 +72,10 @@ struct StepParams {
 // Launch one substep (reads state k&1, writes the other, advances ctrl->k).
 cudaError_t launch_substep(const StepParams &p, cudaStream_t s);
 // The two kernels of a substep separately (with a surface model, the walk
-// leaves the counter to the collision kernel).
+// leaves the counter to the collision kernel).  With p.force set, the "walk"
+// is the atomic spring kernel followed by the per-node integration kernel.
 cudaError_t launch_walk(const StepParams &p, cudaStream_t s);
+cudaError_t launch_atomic_forces_and_integrate(const StepParams &p, cudaStream_t s);
 cudaError_t launch_collide(const StepParams &p, cudaStream_t s);
 
 // A batch of cloths stepped by one persistent walk launch per substep.
@@ -169,6 +172,7 @@ struct ClothHandle {
     float *staging = nullptr;  // 6*n floats for AoS transfers
     int *coll_list = nullptr;  // n entries
     float2 *wind_tab = nullptr; // ny row entries then nx column entries
+    float4 *force = nullptr;    // CLOTH_FLAG_ATOMIC_SPRINGS: pitch*ny force accumulators
     DevGrid grid{};
     bool has_mesh = false;
     StepParams params{};

@@ -723,6 +723,7 @@ cudaError_t launch_k(void (*kern)(KArgs...), int blocks, int threads, cudaStream
 
 cudaError_t launch_walk(const StepParams &p, cudaStream_t s)
 {
+    if (p.force) return launch_atomic_forces_and_integrate(p, s);
     const int warps = p.strips_x * p.strips_y;
     const int blocks = (warps + WARPS_PER_CTA - 1) / WARPS_PER_CTA;
     const bool per = p.ks_slot != nullptr;

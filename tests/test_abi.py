@@ -108,6 +108,20 @@ def test_null_arguments_are_rejected(capi):
     L.cloth_destroy(None)  # NULL-safe
 
 
+def test_batch_rejects_the_atomic_spring_flag_without_gpu(capi):
+    d = (type(_desc(capi)) * 2)(_desc(capi), _desc(capi))
+    d[1].flags = capi.CLOTH_FLAG_ATOMIC_SPRINGS
+    b = C.c_void_p()
+    assert capi.lib().cloth_batch_create(d, 2, None, C.byref(b)) == capi.CLOTH_ERR_INVALID_ARG
+    assert b.value is None
+    assert b"ATOMIC" in capi.lib().cloth_last_error()
+
+
+def test_profile_entry_rejects_bad_arguments(capi):
+    w = C.c_float()
+    assert capi.lib().cloth_profile_substeps(None, 4, C.byref(w), None) == capi.CLOTH_ERR_INVALID_ARG
+
+
 def test_nonfinite_parameters_are_rejected(capi):
     d = _desc(capi)
     d.gravity[1] = float("inf")
