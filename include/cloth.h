@@ -201,6 +201,16 @@ int cloth_query_candidates(ClothHandle *h, const float *S, const float *E, int32
  * and the flag errors of cloth_sync. */
 int cloth_profile_substeps(ClothHandle *h, int32_t nsub, float *walk_us, float *collide_us);
 
+/* Per-vertex normals of the current positions: the normal update that ends
+ * a frame before rendering (Section 3), computed headless.  Each grid quad is
+ * split along its (r,c)-(r+1,c+1) diagonal; a vertex normal is the normalised
+ * sum of the unnormalised face normals of the (up to six) triangles
+ * containing the vertex, the zero vector where that sum is zero.
+ * d_normals: DEVICE pointer to nx*ny*3 floats (node-major, x y z), owned by
+ * the caller; written asynchronously on the handle's stream, after the
+ * substeps already queued.  Errors: CLOTH_ERR_INVALID_ARG (NULL), CLOTH_ERR_CUDA. */
+int cloth_compute_normals(ClothHandle *h, float *d_normals);
+
 /* ---- batches of cloths ------------------------------------------------- */
 
 /* Many independent cloths (each with its own grid, constants, pins and

@@ -19,6 +19,9 @@ Functions (each cites the passage of the paper it follows, see oracle.c):
 * ``adjoint``        reverse mode of ``step`` with the contact set frozen:
                      gradients w.r.t. final-state adjoints of the initial state and
                      of per-spring ks, kd (not in the paper)
+* ``grid_triangles`` / ``normals``  the cloth grid's triangle list and its
+                     per-vertex normals, the update that precedes rendering
+                     (Section 3); plain numpy in double
 """
 from __future__ import annotations
 
@@ -290,3 +293,41 @@ def adjoint(cloth: Cloth, x0, v0, k0: int, nsub: int, lx, lv, grid: Grid | None 
     if rc != 0:
         raise RuntimeError(f"oc_adjoint failed ({rc})")
     return lx.reshape(-1, 3), lv.reshape(-1, 3), gks, gkd
+
+
+# ---------------------------------------------------------------- normals
+# Section 3 ends a frame with a normal vector update before rendering.  The
+# paper does not give the formula; the reading here: each grid quad
+# (r, c), (r, c+1), (r+1, c), (r+1, c+1) is split along its (r, c)-(r+1, c+1)
+# diagonal into (r,c)-(r+1,c)-(r+1,c+1) and (r,c)-(r+1,c+1)-(r,c+1); a vertex
+# normal is the normalised sum of the unnormalised face normals
+# (e1 x e2, so larger faces weigh more) of the triangles that contain it, and
+# the zero vector where that sum is zero.
+
+def grid_triangles(nx: int, ny: int) -> np.ndarray:
+    """Triangles of the cloth grid, [2 (nx-1)(ny-1), 3] node indices, quad by
+    quad in row-major order, two per quad as described above."""
+    tris = []
+    for r in range(ny - 1):
+        for c in range(nx - 1):
+            a, b = r * nx + c, r * nx + c + 1
+            d, e = (r + 1) * nx + c, (r + 1) * nx + c + 1
+            tris.append((a, d, e))
+            tris.append((a, e, b))
+    return np.asarray(tris, dtype=np.int64).reshape(-1, 3)
+
+
+def normals(pos, nx: int, ny: int) -> np.ndarray:
+    """Per-vertex normals [N, 3] (double) of the cloth state pos [N, 3]."""
+    x = np.asarray(pos, dtype=np.float64).reshape(nx * ny, 3)
+    acc = np.zeros_like(x)
+    for a, b, c in grid_triangles(nx, ny):
+        n = np.cross(x[b] - x[a], x[c] - x[a])
+        acc[a] += n
+        acc[b] += n
+        acc[c] += n
+    out = np.zeros_like(acc)
+    ln = np.linalg.norm(acc, axis=1)
+    ok = ln > 0.0
+    out[ok] = acc[ok] / ln[ok, None]
+    return out

@@ -115,6 +115,16 @@ class Cloth:
     def info(self):
         return capi.cloth_get_info(self.h)
 
+    def normals(self, out=None):
+        """Per-vertex normals of the current state as a (N, 3) float32 CUDA
+        tensor (``out`` if given)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.n, 3), dtype=torch.float32, device="cuda")
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == 3 * self.n
+        capi.cloth_compute_normals(self.h, out.data_ptr())
+        return out
+
     def profile_substeps(self, nsub: int):
         """(walk_us, collide_us): mean device time per launch of each kernel."""
         return capi.cloth_profile_substeps(self.h, nsub)

@@ -35,6 +35,7 @@ _NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5
 EXPORTS = ("cloth_create", "cloth_set_mesh", "cloth_step", "cloth_read", "cloth_destroy",
            "cloth_set_state", "cloth_sync", "cloth_last_error", "cloth_get_info", "cloth_get_grid",
            "cloth_query_candidates", "cloth_grid_build_static", "cloth_profile_substeps",
+           "cloth_compute_normals",
            "cloth_batch_create", "cloth_batch_set_mesh", "cloth_batch_step", "cloth_batch_read",
            "cloth_batch_set_state", "cloth_batch_tune", "cloth_batch_set_tuning", "cloth_batch_get_tuning",
            "cloth_batch_sync", "cloth_batch_destroy",
@@ -213,6 +214,11 @@ def cloth_get_info(h: int) -> ClothInfo:
     info = ClothInfo()
     check(lib().cloth_get_info(h, C.byref(info)))
     return info
+
+
+def cloth_compute_normals(h: int, d_normals_ptr: int):
+    """Per-vertex normals into a device buffer of nx*ny*3 floats (async)."""
+    check(lib().cloth_compute_normals(h, C.c_void_p(int(d_normals_ptr))))
 
 
 def cloth_profile_substeps(h: int, nsub: int):

@@ -493,6 +493,19 @@ int cloth_set_state(ClothHandle *h, const float *pos, const float *vel)
     return CLOTH_OK;
 }
 
+int cloth_compute_normals(ClothHandle *h, float *d_normals)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!d_normals) return fail(CLOTH_ERR_INVALID_ARG, "d_normals is NULL");
+    DeviceScope ds(h->device);
+    // the current state buffer: substeps_done counts every substep queued so far
+    const float *cur = h->state + ((h->substeps_done & 1) ? 6 * h->stride : 0);
+    CTRY(h, launch_normals(cur, h->stride, h->desc.nx, h->desc.ny, h->pitch, d_normals, h->sm_count, h->stream),
+         "normals");
+    return CLOTH_OK;
+}
+
 int cloth_profile_substeps(ClothHandle *h, int32_t nsub, float *walk_us, float *collide_us)
 {
     int rc = check_handle(h);

@@ -76,6 +76,10 @@ cudaError_t launch_substep(const StepParams &p, cudaStream_t s);
 // is the atomic spring kernel followed by the per-node integration kernel.
 cudaError_t launch_walk(const StepParams &p, cudaStream_t s);
 cudaError_t launch_atomic_forces_and_integrate(const StepParams &p, cudaStream_t s);
+// Per-vertex normals of the positions in `state` (planes px, py, pz) into
+// out[nx*ny][3].
+cudaError_t launch_normals(const float *state, long long stride, int nx, int ny, int pitch, float *out, int sms,
+                           cudaStream_t s);
 cudaError_t launch_collide(const StepParams &p, cudaStream_t s);
 
 // A batch of cloths stepped by one persistent walk launch per substep.

@@ -452,3 +452,84 @@ def test_literal_lower_bound_lets_resting_nodes_through(oracle_lib):
     grid = oracle_lib.Grid(sc.mesh_verts, sc.mesh_tris)
     x, v = oracle_lib.step(cl, sc.init_pos, sc.init_vel, 0, 300 * sc.substeps, grid)
     assert ray_parity_inside(x, sc.mesh_verts, sc.mesh_tris).sum() > 0
+
+
+# ------------------------------------------------------------- vertex normals
+# Pins of the normal update (Section 3's last step before rendering) against
+# geometry with known normals, not against the oracle's own formula.
+
+def test_normals_of_a_flat_grid_are_the_plane_normal(oracle_lib):
+    # grid along u, v: the face normals are (dv x du)/|.| oriented, every vertex the same
+    nx, ny = 7, 5
+    du, dv = np.array([0.1, 0.0, 0.0]), np.array([0.0, -0.1, 0.0])
+    X = cs.flat_grid(nx, ny, (0.2, 0.3, -0.1), tuple(du), tuple(dv))
+    n = oracle_lib.normals(X, nx, ny)
+    expect = np.cross(dv, du) / np.linalg.norm(np.cross(dv, du))
+    np.testing.assert_allclose(n, np.broadcast_to(expect, n.shape), atol=1e-12)
+
+
+def _surface_errors(oracle_lib, surf, sizes):
+    errs = []
+    for n in sizes:
+        X, exact = surf(n)
+        got = oracle_lib.normals(X, n, n)
+        sgn = np.sign(np.sum(got * exact, axis=1))[:, None]  # orientation is the grid's, not outward
+        inner = np.zeros((n, n), bool)
+        inner[1:-1, 1:-1] = True
+        errs.append(float(np.max(np.linalg.norm(got * sgn - exact, axis=1)[inner.ravel()])))
+    return errs
+
+
+def _cylinder(n, power=1.0):
+    u = np.linspace(0.0, 1.0, n)
+    th = 0.2 + 1.8 * u ** power                # columns: angle
+    z = np.linspace(0.0, 0.5, n)               # rows: height
+    T, Z = np.meshgrid(th, z)
+    X = np.stack([np.cos(T), np.sin(T), Z], -1).reshape(-1, 3)
+    return X, np.stack([np.cos(T), np.sin(T), 0 * T], -1).reshape(-1, 3)
+
+
+def _sphere(n):
+    th = np.linspace(0.4, 1.2, n)              # polar
+    ph = np.linspace(0.3, 1.3, n)              # azimuth
+    TH, PH = np.meshgrid(th, ph)
+    X = np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+    return X, X.copy()
+
+
+def test_normals_of_a_uniform_cylinder_are_radial(oracle_lib):
+    # uniform sampling in angle and height: the two triangles on either side of
+    # a vertex mirror each other, so the area-weighted normal is exactly radial
+    assert max(_surface_errors(oracle_lib, _cylinder, (9, 17))) < 1e-12
+
+
+def test_normals_converge_on_curved_surfaces(oracle_lib):
+    # a sphere: second order (error / 4 per halving of the spacing); a cylinder
+    # sampled non-uniformly in angle: order 1.5 (error / 2.83)
+    e = _surface_errors(oracle_lib, _sphere, (9, 17, 33))
+    assert e[0] < 0.01 and e[0] / e[1] > 3.5 and e[1] / e[2] > 3.5, e
+    e = _surface_errors(oracle_lib, lambda n: _cylinder(n, 1.5), (9, 17, 33))
+    assert e[0] < 0.05 and e[0] / e[1] > 2.6 and e[1] / e[2] > 2.6, e
+
+
+def test_normals_rotate_with_the_cloth_and_ignore_scale(oracle_lib):
+    rng = np.random.default_rng(21)
+    nx, ny = 6, 8
+    X = rng.normal(0, 1, (nx * ny, 3))
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    n0 = oracle_lib.normals(X, nx, ny)
+    np.testing.assert_allclose(oracle_lib.normals(X @ q.T, nx, ny), n0 @ q.T, atol=1e-12)
+    np.testing.assert_allclose(oracle_lib.normals(3.7 * X + 1.0, nx, ny), n0, atol=1e-12)
+    np.testing.assert_allclose(np.linalg.norm(n0, axis=1), 1.0, atol=1e-12)
+
+
+def test_normals_triangle_list_covers_each_quad_once(oracle_lib):
+    nx, ny = 5, 4
+    t = oracle_lib.grid_triangles(nx, ny)
+    assert t.shape == (2 * (nx - 1) * (ny - 1), 3)
+    # every interior vertex belongs to six triangles, corners to one or two
+    deg = np.bincount(t.ravel(), minlength=nx * ny).reshape(ny, nx)
+    assert np.all(deg[1:-1, 1:-1] == 6)
+    assert deg[0, 0] == 2 and deg[-1, -1] == 2 and deg[0, -1] == 1 and deg[-1, 0] == 1
