@@ -19,6 +19,8 @@ Functions (each cites the passage of the paper it follows, see oracle.c):
 * ``adjoint``        reverse mode of ``step`` with the contact set frozen:
                      gradients w.r.t. final-state adjoints of the initial state and
                      of per-spring ks, kd (not in the paper)
+* ``step_edges``     the paper's own narrow phase: cloth-triangle edges at the
+                     updated positions against the surface triangles
 * ``grid_triangles`` / ``normals``  the cloth grid's triangle list and its
                      per-vertex normals, the update that precedes rendering
                      (Section 3); plain numpy in double
@@ -101,6 +103,11 @@ def lib():
             L.oc_step_ex.argtypes = [C.POINTER(OcCloth), C.POINTER(OcMesh), C.POINTER(OcGrid), dp, dp, C.c_int64,
                                      C.c_int32, ip, dp, dp, dp, C.POINTER(C.c_uint64)]
             L.oc_step_ex.restype = C.c_int
+            L.oc_step_edges.argtypes = [C.POINTER(OcCloth), C.POINTER(OcMesh), C.POINTER(OcGrid),
+                                        dp, dp, C.c_int64, C.c_int32, ip]
+            L.oc_step_edges.restype = C.c_int
+            L.oc_edge_affected.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, ip]
+            L.oc_edge_affected.restype = C.c_int32
             L.oc_adjoint.argtypes = [C.POINTER(OcCloth), C.POINTER(OcMesh), C.POINTER(OcGrid), dp, dp, C.c_int64,
                                      C.c_int32, dp, dp, dp, dp]
             L.oc_adjoint.restype = C.c_int
@@ -245,6 +252,35 @@ def step(cloth: Cloth, x, v, k0: int, nsub: int, grid: Grid | None = None, brute
     if want_hits:
         return x.reshape(-1, 3), v.reshape(-1, 3), hits
     return x.reshape(-1, 3), v.reshape(-1, 3)
+
+
+def step_edges(cloth: Cloth, x, v, k0: int, nsub: int, grid: Grid | None = None, brute: bool = False,
+               want_hits: bool = False):
+    """Like ``step`` with the paper's edge-triangle narrow phase: the cloth
+    triangulation's edges at the updated positions against the surface
+    triangles, every vertex of the triangles sharing a hit edge moved from
+    its previous position towards the hit point (stopping delta short),
+    averaged over its hits.  hits: per node, the hits it received."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1).copy()
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1).copy()
+    hits = np.zeros(cloth.N, np.int32)
+    mesh = C.byref(grid.mesh) if grid is not None else None
+    g = C.byref(grid.g) if (grid is not None and not brute) else None
+    rc = lib().oc_step_edges(C.byref(cloth.c), mesh, g, _ptr(x, C.c_double), _ptr(v, C.c_double),
+                             int(k0), int(nsub), _ptr(hits, C.c_int32))
+    if rc != 0:
+        raise RuntimeError(f"oc_step_edges failed ({rc})")
+    if want_hits:
+        return x.reshape(-1, 3), v.reshape(-1, 3), hits
+    return x.reshape(-1, 3), v.reshape(-1, 3)
+
+
+def edge_affected(nx: int, ny: int, r: int, c: int, q: int):
+    """Nodes affected by a hit on edge kind q (0 right, 1 down, 2 diagonal)
+    owned by node (r, c): the vertices of the cloth triangles containing it."""
+    out = np.zeros(4, np.int32)
+    n = lib().oc_edge_affected(nx, ny, r, c, q, _ptr(out, C.c_int32))
+    return sorted(int(a) for a in out[:n])
 
 
 def run(scene, steps: int, grid: Grid | None = None, x=None, v=None, k0: int = 0):

@@ -658,3 +658,146 @@ int oc_adjoint(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, const 
     free(xh); free(vh); free(vph); free(x); free(v); free(lF); free(nlx); free(nlv); free(buf);
     return 0;
 }
+
+/* ------------------------------------- edge-triangle narrow phase (f1) */
+
+/* The paper's own narrow phase (Section 3): triangle-triangle collision
+ * between the cloth at its updated positions and the surface model, by the
+ * extended Moller-Trumbore test of the cloth triangles' edges against the
+ * surface triangles; the nodes "affected by the collision between triangles"
+ * move along "the average value of the direction" (Algorithm 2:
+ * pos = prevPos + responseDirection, vel = -0.5 vel).  The paper gives no
+ * formula for the direction; the reading here, parallel to the point-path
+ * reading of the default narrow phase:
+ *   - the cloth triangles are the grid's quads split along their
+ *     (r,c)-(r+1,c+1) diagonal; the tested edges are the triangulation's
+ *     edges (r,c)-(r,c+1), (r,c)-(r+1,c), (r,c)-(r+1,c+1) at the updated
+ *     positions x*;
+ *   - a hit of edge e at the point P affects every vertex of the (one or
+ *     two) cloth triangles that contain e;
+ *   - an affected free node i gets the direction from its previous position
+ *     towards P, stopping delta short: max(|P - x_i| - delta, 0) (P - x_i)/|P - x_i|
+ *     (zero when P = x_i); the directions of all its hits are averaged.
+ * Free nodes with no hit end at x*; pinned nodes neither move nor receive. */
+
+/* Affected nodes of edge kind q (0: (r,c)-(r,c+1), 1: (r,c)-(r+1,c),
+ * 2: (r,c)-(r+1,c+1)) owned by node (r,c): up to 4 node indices into out;
+ * returns their number (0 when the edge does not exist). */
+int32_t oc_edge_affected(int32_t nx, int32_t ny, int32_t r, int32_t c, int32_t q, int32_t out[4])
+{
+    int32_t n = 0;
+#define OC_NODE(rr, cc) ((int32_t)(rr) * nx + (int32_t)(cc))
+    if (q == 0) {
+        if (c + 1 >= nx) return 0;
+        out[n++] = OC_NODE(r, c);
+        out[n++] = OC_NODE(r, c + 1);
+        if (r + 1 < ny) out[n++] = OC_NODE(r + 1, c + 1); /* second triangle of quad (r, c) */
+        if (r >= 1) out[n++] = OC_NODE(r - 1, c);         /* first triangle of quad (r-1, c) */
+    } else if (q == 1) {
+        if (r + 1 >= ny) return 0;
+        out[n++] = OC_NODE(r, c);
+        out[n++] = OC_NODE(r + 1, c);
+        if (c + 1 < nx) out[n++] = OC_NODE(r + 1, c + 1); /* first triangle of quad (r, c) */
+        if (c >= 1) out[n++] = OC_NODE(r, c - 1);         /* second triangle of quad (r, c-1) */
+    } else {
+        if (r + 1 >= ny || c + 1 >= nx) return 0;
+        out[n++] = OC_NODE(r, c);
+        out[n++] = OC_NODE(r + 1, c + 1);
+        out[n++] = OC_NODE(r + 1, c); /* both triangles of quad (r, c) */
+        out[n++] = OC_NODE(r, c + 1);
+    }
+#undef OC_NODE
+    return n;
+}
+
+/* nsub substeps with the edge-triangle narrow phase; arguments as oc_step.
+ * hits (optional, N ints): number of hits each node received in the last
+ * substep.  Returns 0, or -3 on allocation failure. */
+int oc_step_edges(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, double *x, double *v, int64_t k0,
+                  int32_t nsub, int32_t *hits)
+{
+    const int64_t N = (int64_t)cl->nx * cl->ny;
+    double *A = malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    double *E = malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    double *acc = malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    int32_t *cnt = malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    int32_t *buf = NULL;
+    int64_t bcap = 0;
+    int rc = 0;
+    if (!A || !E || !acc || !cnt) {
+        rc = -3;
+        goto done;
+    }
+    for (int32_t s = 0; s < nsub; s++) {
+        const double t = (double)(k0 + s) * cl->dt_s;
+        oc_accel(cl, x, v, t, A);
+        for (int64_t i = 0; i < N; i++) {
+            const int pinned = cl->pinned && cl->pinned[i];
+            for (int k = 0; k < 3; k++) {
+                if (pinned) {
+                    v[3 * i + k] = 0.0;
+                    E[3 * i + k] = x[3 * i + k];
+                } else {
+                    v[3 * i + k] += cl->dt_s * A[3 * i + k];
+                    E[3 * i + k] = x[3 * i + k] + cl->dt_s * v[3 * i + k];
+                }
+                acc[3 * i + k] = 0.0;
+            }
+            cnt[i] = 0;
+        }
+        if (mesh && mesh->ntris > 0) {
+            for (int32_t r = 0; r < cl->ny; r++)
+                for (int32_t c = 0; c < cl->nx; c++)
+                    for (int32_t q = 0; q < 3; q++) {
+                        int32_t aff[4];
+                        const int32_t na = oc_edge_affected(cl->nx, cl->ny, r, c, q, aff);
+                        if (na == 0) continue;
+                        const int32_t a = r * cl->nx + c;
+                        const int32_t b = q == 0 ? a + 1 : (q == 1 ? a + cl->nx : a + cl->nx + 1);
+                        const double *Sa = E + 3 * (int64_t)a, *Eb = E + 3 * (int64_t)b;
+                        double d[3], L = 0.0;
+                        for (int k = 0; k < 3; k++) { d[k] = Eb[k] - Sa[k]; L += d[k] * d[k]; }
+                        L = sqrt(L);
+                        const int64_t nc = oc_candidates(mesh, grid, Sa, Eb, &buf, &bcap);
+                        for (int64_t j = 0; j < nc; j++) {
+                            const int32_t *tr = mesh->tris + 3 * (int64_t)buf[j];
+                            double V[3][3];
+                            for (int p = 0; p < 3; p++)
+                                for (int k = 0; k < 3; k++) V[p][k] = (double)mesh->verts[3 * (int64_t)tr[p] + k];
+                            double th;
+                            if (!oc_mt(Sa, Eb, V[0], V[1], V[2], cl->eps, cl->t_min, &th)) continue;
+                            double P[3];
+                            for (int k = 0; k < 3; k++) P[k] = Sa[k] + th * (d[k] / L);
+                            for (int32_t m = 0; m < na; m++) {
+                                const int32_t i = aff[m];
+                                if (cl->pinned && cl->pinned[i]) continue;
+                                double w[3], lw = 0.0;
+                                for (int k = 0; k < 3; k++) { w[k] = P[k] - x[3 * (int64_t)i + k]; lw += w[k] * w[k]; }
+                                lw = sqrt(lw);
+                                const double sc = lw > 0.0 ? (lw - cl->delta > 0.0 ? lw - cl->delta : 0.0) / lw : 0.0;
+                                for (int k = 0; k < 3; k++) acc[3 * (int64_t)i + k] += sc * w[k];
+                                cnt[i]++;
+                            }
+                        }
+                    }
+        }
+        for (int64_t i = 0; i < N; i++) {
+            if (cnt[i] > 0) {
+                for (int k = 0; k < 3; k++) {
+                    x[3 * i + k] += acc[3 * i + k] / (double)cnt[i];
+                    v[3 * i + k] *= cl->restitution;
+                }
+            } else {
+                for (int k = 0; k < 3; k++) x[3 * i + k] = E[3 * i + k];
+            }
+            if (hits) hits[i] = cnt[i];
+        }
+    }
+done:
+    free(A);
+    free(E);
+    free(acc);
+    free(cnt);
+    free(buf);
+    return rc;
+}

@@ -533,3 +533,89 @@ def test_normals_triangle_list_covers_each_quad_once(oracle_lib):
     deg = np.bincount(t.ravel(), minlength=nx * ny).reshape(ny, nx)
     assert np.all(deg[1:-1, 1:-1] == 6)
     assert deg[0, 0] == 2 and deg[-1, -1] == 2 and deg[0, -1] == 1 and deg[-1, 0] == 1
+
+
+# ------------------------------------------- edge-triangle narrow phase (f1)
+# Pins of the oracle's reading of the paper's own narrow phase: cloth
+# triangle edges at the updated positions against the surface triangles.
+
+def test_edge_affected_sets_are_the_vertices_of_the_triangles_sharing_the_edge(oracle_lib):
+    nx, ny = 5, 4
+    tris = oracle_lib.grid_triangles(nx, ny)
+    from collections import defaultdict
+    by_edge = defaultdict(set)
+    for t in tris:
+        for a, b in ((t[0], t[1]), (t[1], t[2]), (t[0], t[2])):
+            by_edge[(min(a, b), max(a, b))].update(int(u) for u in t)
+    seen = 0
+    for r in range(ny):
+        for c in range(nx):
+            for q, (dr, dc) in enumerate(((0, 1), (1, 0), (1, 1))):
+                aff = oracle_lib.edge_affected(nx, ny, r, c, q)
+                r2, c2 = r + dr, c + dc
+                if r2 >= ny or c2 >= nx:
+                    assert aff == []
+                    continue
+                e = (r * nx + c, r2 * nx + c2)
+                assert aff == sorted(by_edge[e]), (r, c, q)
+                seen += 1
+    assert seen == len(by_edge)  # every edge of the triangulation, once
+
+
+def _edge_scene(nx, ny, pos, vel, **kw):
+    return make_scene(nx, ny, pos=pos, vel=vel, mesh=floor_mesh(), dt=1e-3, substeps=1, **kw)
+
+
+def test_edge_phase_closed_form_single_edge_through_a_floor(oracle_lib):
+    # two free nodes, no forces: the edge A*->B* crosses y = 0 at its midpoint
+    # P; each node moves from its previous position towards P, stopping delta
+    # short, and its velocity is scaled by -0.5 (Algorithm 2)
+    pos = np.array([[0.3, 0.003, 0.3], [0.35, 0.003, 0.3]], np.float32)
+    vel = np.array([[0.0, -2.0, 0.0], [0.0, -4.0, 0.0]], np.float32)
+    sc = _edge_scene(2, 1, pos, vel)
+    grid = oracle_lib.Grid(*floor_mesh())
+    x, v, hits = oracle_lib.step_edges(oracle_lib.Cloth(sc), pos, vel, 0, 1, grid, want_hits=True)
+    X = pos.astype(np.float64)
+    Es = X + 1e-3 * vel.astype(np.float64)
+    P = Es[0] + (Es[1] - Es[0]) * (Es[0, 1] / (Es[0, 1] - Es[1, 1]))
+    for i in range(2):
+        w = P - X[i]
+        lw = np.linalg.norm(w)
+        np.testing.assert_allclose(x[i], X[i] + (lw - 1e-4) / lw * w, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(v[i], -0.5 * vel[i].astype(np.float64), rtol=0, atol=1e-12)
+    assert list(hits) == [1, 1]
+
+
+def test_edge_phase_grid_equals_all_pairs_and_no_mesh_equals_plain_step(oracle_lib):
+    rng = np.random.default_rng(31)
+    nx, ny = 9, 7
+    X0 = cs.flat_grid(nx, ny, (0.2, 0.004, 0.25), (0.05, 0.0, 0.0), (0.0, 0.0, 0.06))
+    pos = (X0 + rng.uniform(-0.003, 0.003, X0.shape)).astype(np.float32)
+    vel = rng.normal(0.0, 3.0, X0.shape).astype(np.float32)
+    vel[:, 1] -= 5.0
+    sc = _edge_scene(nx, ny, pos, vel, ks=(50.0, 30.0, 10.0), kd=(0.1, 0.1, 0.1), gravity=(0, -9.81, 0))
+    grid = oracle_lib.Grid(*floor_mesh())
+    cl = oracle_lib.Cloth(sc)
+    a = oracle_lib.step_edges(cl, pos, vel, 0, 1, grid, want_hits=True)
+    b = oracle_lib.step_edges(cl, pos, vel, 0, 1, grid, brute=True, want_hits=True)
+    assert int(a[2].sum()) > 10
+    for u, w in zip(a, b):
+        assert np.array_equal(u, w)
+    c = oracle_lib.step_edges(cl, pos, vel, 0, 3, None)
+    d = oracle_lib.step(cl, pos, vel, 0, 3, None)
+    for u, w in zip(c, d):
+        assert np.array_equal(u, w)
+
+
+def test_edge_phase_does_not_see_edges_parallel_to_the_surface(oracle_lib):
+    # the method's blind spot (extended MT rejects |a| < eps): a flat cloth
+    # that crosses a floor parallel to it keeps every edge parallel to the
+    # floor, so no hit is found and the cloth passes through
+    nx = ny = 3
+    pos = cs.flat_grid(nx, ny, (0.3, 0.001, 0.3), (0.05, 0.0, 0.0), (0.0, 0.0, 0.05)).astype(np.float32)
+    vel = np.zeros_like(pos)
+    vel[:, 1] = -2.0
+    sc = _edge_scene(nx, ny, pos, vel)
+    x, _, hits = oracle_lib.step_edges(oracle_lib.Cloth(sc), pos, vel, 0, 1, oracle_lib.Grid(*floor_mesh()),
+                                       want_hits=True)
+    assert hits.sum() == 0 and np.all(x[:, 1] < 0.0)
