@@ -366,6 +366,42 @@ def run_atomic_ab(stream, flush, steps: int = 100):
     return out
 
 
+def run_edge_ab(stream, flush, warm: int = 150, steps: int = 100):
+    """The paper's own narrow phase (cloth-triangle edges against the surface,
+    CLOTH_FLAG_EDGE_COLLISION) against the default node-path narrow phase on
+    the 256x256 cloth over the 81,920-triangle mesh: steps `warm`..`warm+steps`
+    (the cloth lands on the mesh), L2 flushed before each step."""
+    import torch
+
+    import cloth_scenes as cs
+    import paper_2507_11794_gb300 as P
+    sc = cs.config2()
+    out = {"workload": f"256x256 cloth (65,536 nodes) over the 81,920-triangle displaced icosphere, steps "
+                       f"{warm}-{warm + steps} (contact), dt=1/1200 s, 4 substeps, L2 flushed per step"}
+    for name, flags in (("node_paths", 0), ("edges", P.capi.CLOTH_FLAG_EDGE_COLLISION)):
+        cl = P.Cloth(sc, stream=int(stream.cuda_stream), flags=flags)
+        cl.step(warm)
+        cl.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            cl.step(1)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        w = c = 0.0
+        for i in range(10):
+            flush.fill_(float(i))
+            wi, ci = cl.profile_substeps(sc.substeps)
+            w += wi / 10
+            c += ci / 10
+        cl.close()
+        out[name] = {"ms_per_step": ms, "node_steps_per_s": sc.n / (ms / 1e3), "walk_us_per_substep": w,
+                     "collision_us_per_substep": c}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -455,6 +491,7 @@ def run_ours(args):
     batch = None if args.no_batch else run_batch(args, stream)
     adjoint = None if args.no_batch else run_adjoint(stream)
     atomic_ab = None if args.no_batch else run_atomic_ab(stream, flush)
+    edge_ab = None if args.no_batch else run_edge_ab(stream, flush)
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -486,7 +523,8 @@ def run_ours(args):
            "roofline": roofline, "cpu_baseline": cpu,
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 12 * N,
                    "d2h_bytes_per_step": 2 * 12 * N, "steps": ke},
-           "gpu_launches": launches, "clocks": clocks.summary(), "batch": batch, "adjoint": adjoint, "atomic_springs_ab": atomic_ab, "normals": normals,
+           "gpu_launches": launches, "clocks": clocks.summary(), "batch": batch, "adjoint": adjoint, "atomic_springs_ab": atomic_ab, "edge_narrow_phase_ab": edge_ab,
+           "normals": normals,
            "wall_s_timed_loop": wall}
     print(json.dumps(out), flush=True)
     if pg is not None:

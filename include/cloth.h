@@ -67,6 +67,19 @@ enum {
  * vary from run to run.  Kept as an A/B of the paper's design against the
  * default fused column walk.  Not accepted by cloth_batch_create. */
 #define CLOTH_FLAG_ATOMIC_SPRINGS 2u
+/* The paper's own narrow phase instead of the node-path test: the edges of
+ * the cloth triangles (the grid's quads split along their (r,c)-(r+1,c+1)
+ * diagonal) at the updated positions are tested against the surface
+ * triangles with the extended Moller-Trumbore test (Section 3); every vertex
+ * of the cloth triangles sharing a hit edge moves from its previous position
+ * towards the hit point, stopping contact_offset short, averaged over its
+ * hits, and its velocity is scaled by restitution (Algorithm 2).  Nodes are
+ * considered if their updated position lies within twice the rest diagonal of
+ * the mesh's grid, so edges are assumed to stay under twice their rest length
+ * within a substep.  Edges parallel to the surface are not detected (the
+ * test's parallel rule).  Not accepted by cloth_batch_create or
+ * cloth_rollout_create. */
+#define CLOTH_FLAG_EDGE_COLLISION 4u
 
 /* Sinusoidal external acceleration field (N/kg) added to gravity:
  *   w(X0, t) = amp * dir * sin(2*pi*freq*t + kappa*(udir . X0) + phase),

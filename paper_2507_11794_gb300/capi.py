@@ -27,6 +27,7 @@ CLOTH_ERR_BAD_MESH = -6
 CLOTH_ERR_STATE = -7
 CLOTH_FLAG_NO_GRAPH = 1
 CLOTH_FLAG_ATOMIC_SPRINGS = 2
+CLOTH_FLAG_EDGE_COLLISION = 4
 
 _NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT",
           -6: "BAD_MESH", -7: "STATE"}

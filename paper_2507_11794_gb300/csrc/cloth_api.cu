@@ -82,6 +82,8 @@ void free_all(ClothHandle *h)
     h->wind_tab = nullptr;
     cudaFree(h->force);
     h->force = nullptr;
+    cudaFree(h->edge_resp);
+    h->edge_resp = nullptr;
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->state = nullptr;
     h->pin_bits = nullptr;
@@ -156,9 +158,13 @@ void cloth_fill_params(ClothHandle *h)
     for (int a = 0; a < 3; a++) {
         // box of the non-border cells 1..dims-2 (border cells hold no triangle),
         // widened by 1% of a cell against rounding of the cell formula
-        p.mlo[a] = h->has_mesh ? (float)((double)h->grid.origin[a] + 0.99 * (double)h->grid.h) : 0.0f;
-        p.mhi[a] = h->has_mesh ? (float)((double)h->grid.origin[a] + ((double)h->grid.dims[a] - 0.99) * h->grid.h)
-                               : 0.0f;
+        // the edge narrow phase also needs the nodes of cloth triangles whose
+        // edges reach those cells: widen by twice the rest diagonal
+        const double m = (d.flags & CLOTH_FLAG_EDGE_COLLISION) ? 2.0 * (double)p.L0[2] : 0.0;
+        p.mlo[a] = h->has_mesh ? (float)((double)h->grid.origin[a] + 0.99 * (double)h->grid.h - m) : 0.0f;
+        p.mhi[a] = h->has_mesh
+                       ? (float)((double)h->grid.origin[a] + ((double)h->grid.dims[a] - 0.99) * h->grid.h + m)
+                       : 0.0f;
     }
     p.delta = d.contact_offset;
     p.eps = d.mt_eps;
@@ -166,6 +172,7 @@ void cloth_fill_params(ClothHandle *h)
     p.restitution = d.restitution;
     p.ctrl = h->ctrl;
     p.force = h->force;
+    p.edge_resp = h->edge_resp;
     p.coll_list = h->coll_list;
     p.coll_count = h->ctrl ? &h->ctrl->coll_count : nullptr;
     p.coll_blocks = h->sm_count * CLOTH_COLL_CTAS_PER_SM;
@@ -330,6 +337,9 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
                     break;
             }
         }
+        if ((d.flags & CLOTH_FLAG_EDGE_COLLISION) &&
+            (e = cudaMalloc(&h->edge_resp, sizeof(float4) * (size_t)N)) != cudaSuccess)
+            break;
         if (d.flags & CLOTH_FLAG_ATOMIC_SPRINGS) {
             const size_t nf = (size_t)h->pitch * d.ny;
             if ((e = cudaMalloc(&h->force, sizeof(float4) * nf)) != cudaSuccess) break;

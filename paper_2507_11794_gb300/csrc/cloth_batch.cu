@@ -176,8 +176,9 @@ int cloth_batch_create(const ClothDesc *descs, int32_t count, void *stream, Clot
     *out = nullptr;
     if (!descs || count < 1) return bfail(CLOTH_ERR_INVALID_ARG, "need at least one description");
     for (int i = 0; i < count; i++)
-        if (descs[i].flags & CLOTH_FLAG_ATOMIC_SPRINGS)
-            return bfail(CLOTH_ERR_INVALID_ARG, "CLOTH_FLAG_ATOMIC_SPRINGS is not supported in batches");
+        if (descs[i].flags & (CLOTH_FLAG_ATOMIC_SPRINGS | CLOTH_FLAG_EDGE_COLLISION))
+            return bfail(CLOTH_ERR_INVALID_ARG,
+                         "CLOTH_FLAG_ATOMIC_SPRINGS and CLOTH_FLAG_EDGE_COLLISION are not supported in batches");
     for (int i = 1; i < count; i++)
         if (descs[i].dt != descs[0].dt || descs[i].substeps != descs[0].substeps)
             return bfail(CLOTH_ERR_INVALID_ARG, "every cloth of a batch needs the same dt and substeps (cloth %d)", i);

@@ -284,3 +284,184 @@ __device__ __forceinline__ void collide_list(const Src &src, CollShared &sh, uns
         }
     }
 }
+
+// ------------------------------------------- edge-triangle narrow phase
+// The paper's own narrow phase (Section 3): edges of the cloth triangles (the
+// grid's quads split along their (r,c)-(r+1,c+1) diagonal) at the updated
+// positions against the surface triangles.  A hit of an edge at P affects
+// every vertex of the cloth triangles that share the edge; an affected free
+// node i gets the direction from its previous position S_i towards P,
+// stopping delta short, max(|P - S_i| - delta, 0) (P - S_i)/|P - S_i|, and
+// moves by the mean over its hits (Algorithm 2).  Gathered per node: the 12
+// edges whose triangles contain node (r, c), each as (owner endpoint ->
+// other endpoint) with the owner the edge's upper-left node, the orientation
+// the test's arithmetic is defined in.
+struct EdgeOfs {
+    signed char ar, ac, br, bc;
+};
+__device__ __forceinline__ EdgeOfs edge_of_node(int q)
+{
+    // (0,+1) edges: own, left, up-left row above, row below
+    // (+1,0) edges: own, above, up-left column, right column
+    // (+1,+1) edges: own, up-left, the two that have (r,c) as opposite vertex
+    switch (q) {
+    case 0: return {0, 0, 0, 1};
+    case 1: return {0, -1, 0, 0};
+    case 2: return {-1, -1, -1, 0};
+    case 3: return {1, 0, 1, 1};
+    case 4: return {0, 0, 1, 0};
+    case 5: return {-1, 0, 0, 0};
+    case 6: return {-1, -1, 0, -1};
+    case 7: return {0, 1, 1, 1};
+    case 8: return {0, 0, 1, 1};
+    case 9: return {-1, -1, 0, 0};
+    case 10: return {-1, 0, 0, 1};
+    default: return {0, -1, 1, 0};
+    }
+}
+constexpr int EDGES_PER_NODE = 12;
+
+struct EdgeShared {
+    CollLane lane[COLL_WARPS][32];
+    int base[COLL_WARPS][32];
+    float4 hit[COLL_WARPS][32];  // one round's results: hit point P and 1, or w = 0
+};
+
+// One warp's pass over 32 list entries per round; writes the response of
+// entry i to p.edge_resp[i] as (position, 1) or (0, 0, 0, 0) without a hit.
+__device__ __forceinline__ void collide_edges_list(const StepParams &p, EdgeShared &sh, unsigned long long k,
+                                                   unsigned n)
+{
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned long long nw = (unsigned long long)gridDim.x * COLL_WARPS;
+    const unsigned long long w = (unsigned long long)blockIdx.x * COLL_WARPS + wib;
+    CollLane &me = sh.lane[wib][lane];
+    const long long st = p.stride;
+    const float *in = (k & 1ull) ? p.state1 : p.state0;
+    const float *xs = (k & 1ull) ? p.state0 : p.state1;  // updated positions (written by the walk)
+    for (unsigned long long b0 = 0; b0 < n; b0 += 32ull * nw) {
+        const unsigned long long i = b0 + (unsigned long long)lane * nw + w;
+        const bool valid = i < n;
+        int r = 0, c = 0;
+        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+        if (valid) {
+            const int o = __ldg(p.coll_list + i);
+            r = o / p.pitch;
+            c = o - r * p.pitch;
+            sx = __ldg(in + o);
+            sy = __ldg(in + st + o);
+            sz = __ldg(in + 2 * st + o);
+        }
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;  // sum of directions
+        int K = 0;
+        for (int q = 0; q < EDGES_PER_NODE; q++) {
+            int cnt = 0;
+            if (valid) {
+                const EdgeOfs e = edge_of_node(q);
+                const int ra = r + e.ar, ca = c + e.ac, rb = r + e.br, cb = c + e.bc;
+                if (ra >= 0 && ca >= 0 && rb < p.ny && cb < p.nx && ca < p.nx && cb >= 0) {
+                    const long long oa = (long long)ra * p.pitch + ca, ob = (long long)rb * p.pitch + cb;
+                    const float x0 = xs[oa], y0 = xs[st + oa], z0 = xs[2 * st + oa];
+                    const float x1 = xs[ob], y1 = xs[st + ob], z1 = xs[2 * st + ob];
+                    CollPath path;
+                    if (coll_path(p, x0, y0, z0, x1, y1, z1, path)) {
+                        const CollBox bx = coll_box(p, x0, y0, z0, x1, y1, z1);
+                        const int nxc = bx.hix - bx.lox + 1, nyc = bx.hiy - bx.loy + 1, nzc = bx.hiz - bx.loz + 1;
+                        if ((long long)nxc * nyc * nzc <= COLL_MAXC) {
+                            int cc = 0;
+                            for (int cz = bx.loz; cz <= bx.hiz; cz++)
+                                for (int cy = bx.loy; cy <= bx.hiy; cy++)
+                                    for (int cx = bx.lox; cx <= bx.hix; cx++, cc++) {
+                                        const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
+                                        const int e0 = __ldg(p.cell_start + cell), e1 = __ldg(p.cell_start + cell + 1);
+                                        cnt += e1 - e0;
+                                        me.cell[cc] = make_int2(e0, cnt);
+                                    }
+                            me.s = make_float4(path.sx, path.sy, path.sz, path.L);
+                            me.r = make_float4(path.rx, path.ry, path.rz, 0.0f);
+                            me.box = make_int4(bx.lox, bx.loy, bx.loz, nxc | (nyc << 16));
+                        } else {
+                            // an edge spanning more than COLL_MAXC cells: this lane
+                            // walks its candidates alone, in the same order
+                            for (int cz = bx.loz; cz <= bx.hiz; cz++)
+                                for (int cy = bx.loy; cy <= bx.hiy; cy++)
+                                    for (int cx = bx.lox; cx <= bx.hix; cx++) {
+                                        const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
+                                        const int e0 = __ldg(p.cell_start + cell), e1 = __ldg(p.cell_start + cell + 1);
+                                        for (int ee = e0; ee < e1; ee++) {
+                                            float th, f;
+                                            float4 A, B, C;
+                                            if (!coll_candidate(p, path, ee, cx, cy, cz, bx.lox, bx.loy, bx.loz, th, f,
+                                                                A, B, C))
+                                                continue;
+                                            const float wx = path.sx + th * path.rx - sx;
+                                            const float wy = path.sy + th * path.ry - sy;
+                                            const float wz = path.sz + th * path.rz - sz;
+                                            const float lw = sqrtf(wx * wx + wy * wy + wz * wz);
+                                            const float sc = lw > 0.0f ? fmaxf(lw - p.delta, 0.0f) / lw : 0.0f;
+                                            ax += sc * wx;
+                                            ay += sc * wy;
+                                            az += sc * wz;
+                                            K++;
+                                        }
+                                    }
+                        }
+                    }
+                }
+            }
+            int incl = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += t;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int excl = incl - cnt;
+            sh.base[wib][lane] = excl;
+            __syncwarp();
+            for (int r0 = 0; r0 < total; r0 += 32) {
+                const int j = r0 + lane;
+                float4 hv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (j < total) {
+                    int ow = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (sh.base[wib][ow + step] <= j) ow += step;
+                    const CollLane &L = sh.lane[wib][ow];
+                    const int loc = j - sh.base[wib][ow];
+                    int cc = 0;
+                    while (L.cell[cc].y <= loc) cc++;
+                    const long long e = L.cell[cc].x + (loc - (cc ? L.cell[cc - 1].y : 0));
+                    const int nxc = L.box.w & 0xffff, nyc = L.box.w >> 16;
+                    const int cx = L.box.x + cc % nxc, cy = L.box.y + (cc / nxc) % nyc, cz = L.box.z + cc / (nxc * nyc);
+                    const CollPath lq = {L.s.x, L.s.y, L.s.z, L.r.x, L.r.y, L.r.z, L.s.w};
+                    float th, f;
+                    float4 A, B, C;
+                    if (coll_candidate(p, lq, e, cx, cy, cz, L.box.x, L.box.y, L.box.z, th, f, A, B, C))
+                        hv = make_float4(lq.sx + th * lq.rx, lq.sy + th * lq.ry, lq.sz + th * lq.rz, 1.0f);
+                }
+                sh.hit[wib][lane] = hv;
+                __syncwarp();
+                if (cnt > 0) {
+                    const int q0 = max(excl, r0), q1 = min(excl + cnt, r0 + 32);
+                    for (int t = q0; t < q1; t++) {
+                        const float4 P = sh.hit[wib][t - r0];
+                        if (P.w == 0.0f) continue;
+                        const float wx = P.x - sx, wy = P.y - sy, wz = P.z - sz;
+                        const float lw = sqrtf(wx * wx + wy * wy + wz * wz);
+                        const float sc = lw > 0.0f ? fmaxf(lw - p.delta, 0.0f) / lw : 0.0f;
+                        ax += sc * wx;
+                        ay += sc * wy;
+                        az += sc * wz;
+                        K++;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (valid) {
+            p.edge_resp[i] = K > 0 ? make_float4(sx + ax / (float)K, sy + ay / (float)K, sz + az / (float)K, 1.0f)
+                                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    }
+}

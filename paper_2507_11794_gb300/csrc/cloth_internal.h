@@ -58,6 +58,7 @@ struct StepParams {
     int *coll_cloth;           // batch mode: cloth index of each entry (nullptr for one cloth)
     float *vstar;              // optional 3 planes: velocity after integration (adjoint recompute)
     float4 *force;             // per-node force buffer of the atomic spring path, or nullptr
+    float4 *edge_resp;         // edge narrow phase: per list entry (response position, hit flag), or nullptr
     unsigned *coll_count;      // entries in coll_list (reset by the collision kernel)
     int coll_blocks;           // CTAs of the collision kernel
     float delta, eps, tmin, restitution;
@@ -177,6 +178,7 @@ struct ClothHandle {
     int *coll_list = nullptr;  // n entries
     float2 *wind_tab = nullptr; // ny row entries then nx column entries
     float4 *force = nullptr;    // CLOTH_FLAG_ATOMIC_SPRINGS: pitch*ny force accumulators
+    float4 *edge_resp = nullptr; // CLOTH_FLAG_EDGE_COLLISION: n response slots (one per list entry)
     DevGrid grid{};
     bool has_mesh = false;
     StepParams params{};

@@ -538,6 +538,67 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kern
     }
 }
 
+// Edge narrow phase (CLOTH_FLAG_EDGE_COLLISION): responses are computed from
+// the updated positions of all listed nodes' neighbours, so they go to a
+// scratch array first and a second kernel applies them.
+__global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_edges_kernel(const __grid_constant__ StepParams p)
+{
+    __shared__ EdgeShared sh;
+    __shared__ unsigned long long s_k;
+    __shared__ unsigned s_n;
+    pdl_launch_dependents();
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        s_k = *(volatile unsigned long long *)&p.ctrl->k;
+        s_n = *(volatile unsigned *)p.coll_count;
+    }
+    __syncthreads();
+    collide_edges_list(p, sh, s_k, s_n);
+}
+
+__global__ void __launch_bounds__(256) edge_apply_kernel(const __grid_constant__ StepParams p)
+{
+    __shared__ unsigned long long s_k;
+    __shared__ unsigned s_n;
+    pdl_launch_dependents();
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        s_k = *(volatile unsigned long long *)&p.ctrl->k;
+        s_n = *(volatile unsigned *)p.coll_count;
+    }
+    __syncthreads();
+    const unsigned long long k = s_k;
+    float *out = (k & 1ull) ? p.state0 : p.state1;
+    const long long st = p.stride;
+    float fsum = 0.0f;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < s_n; i += gridDim.x * blockDim.x) {
+        const float4 e = p.edge_resp[i];
+        if (e.w == 0.0f) continue;
+        const int o = __ldg(p.coll_list + i);
+        out[o] = e.x;
+        out[st + o] = e.y;
+        out[2 * st + o] = e.z;
+        out[3 * st + o] *= p.restitution;
+        out[4 * st + o] *= p.restitution;
+        out[5 * st + o] *= p.restitution;
+        fsum += e.x + e.y + e.z;
+    }
+    if (__any_sync(FULL, !isfinite(fsum)) && (threadIdx.x & 31) == 0)
+        atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // the last CTA resets the list and advances the substep counter
+        __threadfence();
+        const unsigned prev = atomicAdd(&p.ctrl->blocks_done, 1u);
+        if (prev == gridDim.x - 1) {
+            p.ctrl->blocks_done = 0;
+            *p.coll_count = 0u;
+            p.ctrl->k = k + 1;
+            __threadfence();
+        }
+    }
+}
+
 // ---------------------------------------------------------------- batches
 // Persistent walk over a list of (cloth, strip) items of many cloths: each
 // warp takes the next item from a device counter (items sorted longest
@@ -737,6 +798,11 @@ cudaError_t launch_walk(const StepParams &p, cudaStream_t s)
 
 cudaError_t launch_collide(const StepParams &p, cudaStream_t s)
 {
+    if (p.edge_resp) {
+        cudaError_t e = launch_k(collide_edges_kernel, p.coll_blocks, 32 * COLL_WARPS, s, p);
+        if (e != cudaSuccess) return e;
+        return launch_k(edge_apply_kernel, p.coll_blocks, 256, s, p);
+    }
     return launch_k(collide_kernel, p.coll_blocks, 32 * COLL_WARPS, s, p);
 }
 
