@@ -402,6 +402,33 @@ def run_edge_ab(stream, flush, warm: int = 150, steps: int = 100):
     return out
 
 
+def run_pulling(stream, flush, warm: int = 150, steps: int = 150):
+    """The paper's second experiment: a 256x256 cloth (65,536 nodes) pulled
+    by its pinned leading row at 0.5 m/s across the 81,920-triangle model;
+    steps warm..warm+steps (the cloth slides over the model), L2 flushed
+    before each step."""
+    import torch
+
+    import cloth_scenes as cs
+    import paper_2507_11794_gb300 as P
+    sc = cs.pulling_scene(256, "l6")
+    cl = P.Cloth(sc, stream=int(stream.cuda_stream))
+    cl.step(warm)
+    cl.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        cl.step(1)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    cl.close()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    return {"workload": f"256x256 cloth (65,536 nodes) pulled at 0.5 m/s across the 81,920-triangle model, steps "
+                        f"{warm}-{warm + steps}, dt=1/1200 s in 4 substeps, L2 flushed per step",
+            "ms_per_step": ms, "node_steps_per_s": sc.n / (ms / 1e3), "steps_per_s": 1e3 / ms}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -492,6 +519,7 @@ def run_ours(args):
     adjoint = None if args.no_batch else run_adjoint(stream)
     atomic_ab = None if args.no_batch else run_atomic_ab(stream, flush)
     edge_ab = None if args.no_batch else run_edge_ab(stream, flush)
+    pulling = None if args.no_batch else run_pulling(stream, flush)
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -523,7 +551,7 @@ def run_ours(args):
            "roofline": roofline, "cpu_baseline": cpu,
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 12 * N,
                    "d2h_bytes_per_step": 2 * 12 * N, "steps": ke},
-           "gpu_launches": launches, "clocks": clocks.summary(), "batch": batch, "adjoint": adjoint, "atomic_springs_ab": atomic_ab, "edge_narrow_phase_ab": edge_ab,
+           "gpu_launches": launches, "clocks": clocks.summary(), "batch": batch, "adjoint": adjoint, "atomic_springs_ab": atomic_ab, "edge_narrow_phase_ab": edge_ab, "pulling_scene": pulling,
            "normals": normals,
            "wall_s_timed_loop": wall}
     print(json.dumps(out), flush=True)

@@ -213,6 +213,7 @@ class Scene:
     mt_t_min: float = 0.0      # hit distance bound t_min < t < |d|
     restitution: float = -0.5
     wind: Wind = dataclasses.field(default_factory=Wind)
+    pin_velocity: Tuple[float, float, float] = (0.0, 0.0, 0.0)  # pinned nodes move at this velocity (m/s)
 
     @property
     def n(self) -> int:
@@ -292,6 +293,30 @@ def config2(steps: int = 1000, mesh=None) -> Scene:
     return Scene("config2_256x256_L6", n, n, o, du, dv, 1.0, ks, kd, (0.0, -9.81, 0.0),
                  1.0 / 1200.0, 4, steps, pos, np.zeros_like(pos),
                  np.zeros(n * n, np.uint8), mv, mt)
+
+
+def pulling_scene(n: int = 128, mesh: str = "sphere", steps: int = 600, speed: float = 0.5) -> Scene:
+    """The paper's second experiment (Section 4, Fig. 5): a cloth pulled
+    across a 3D model.  n x n cloth, 1 m x 1 m, horizontal at y = 0.3 above a
+    model of radius 0.25 at the origin; its leading row (z = -0.5) is pinned
+    and pulled along +x at `speed` m/s (kinematic pins) while gravity drapes
+    the rest over the model.  mesh: 'sphere' (5,120-triangle icosphere) or
+    'l6' (the 81,920-triangle displaced mesh scaled to radius 0.25); dt 1/1200 s
+    in 4 substeps."""
+    o, du, dv = _square_horizontal(n, 0.3)
+    pos = flat_grid(n, n, o, du, dv).astype(np.float32)
+    pinned = np.zeros(n * n, np.uint8)
+    pinned[:n] = 1
+    ks, kd = scaled_constants(n)
+    if mesh == "sphere":
+        mv, mt = sphere_mesh(4, 0.25, (0.0, 0.0, 0.0))
+    elif mesh == "l6":
+        mv, mt = displaced_mesh_l6(0)
+        mv = (mv * np.float32(0.25 / 0.45)).astype(np.float32)
+    else:
+        raise ValueError(mesh)
+    return Scene(f"pulling_{n}x{n}_{mesh}", n, n, o, du, dv, 1.0, ks, kd, (0.0, -9.81, 0.0), 1.0 / 1200.0, 4,
+                 steps, pos, np.zeros_like(pos), pinned, mv, mt, pin_velocity=(speed, 0.0, 0.0))
 
 
 def wind_config3() -> Wind:

@@ -121,6 +121,9 @@ typedef struct ClothDesc {
     float restitution;       /* velocity factor on contact (Algorithm 2: -0.5) */
     ClothWind wind;
     uint32_t flags;          /* CLOTH_FLAG_* */
+    float pin_velocity[3];   /* m/s: pinned nodes move kinematically,
+                                x += dt_s*pin_velocity, v = pin_velocity (the
+                                paper's pulling scene); 0 = fixed pins */
 } ClothDesc;
 
 /* Canonical spring order (for ks_spring / kd_spring): nodes in row-major

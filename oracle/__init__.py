@@ -64,6 +64,7 @@ class OcCloth(C.Structure):
         ("delta", C.c_double), ("eps", C.c_double), ("t_min", C.c_double), ("restitution", C.c_double),
         ("wind_amp", C.c_double), ("wind_dir", C.c_double * 3), ("wind_udir", C.c_double * 3),
         ("wind_freq", C.c_double), ("wind_kappa", C.c_double), ("wind_phase", C.c_double),
+        ("pin_vel", C.c_double * 3),
     ]
 
 
@@ -147,6 +148,8 @@ class Cloth:
         c.t_min = float(s.mt_t_min)
         c.wind_amp, c.wind_freq = float(s.wind.amp), float(s.wind.freq)
         c.wind_kappa, c.wind_phase = float(s.wind.kappa), float(s.wind.phase)
+        for k in range(3):
+            c.pin_vel[k] = float(getattr(s, "pin_velocity", (0.0, 0.0, 0.0))[k])
         self.c = c
 
 

@@ -20,7 +20,9 @@
  *      Force[a] += F, Force[b] -= F, springs taken in canonical order;
  *   2. "the Euler method" with spring force, gravity and external force
  *      (Section 3), read as symplectic Euler: v += dt_s*(F/m + g + w),
- *      x* = x + dt_s*v; pinned nodes keep x and get v = 0;
+ *      x* = x + dt_s*v; pinned nodes move kinematically at the prescribed pin
+ *      velocity u (x += dt_s*u, v = u; u = 0: fixed pins, the paper's hanging
+ *      cloth; u != 0: its pulling scene);
  *   3. collision of the segment x -> x* of every free node with the static
  *      surface triangles by the extended Moller-Trumbore test (Section 3,
  *      "Extended Moller-Trumbore Process"), candidates from a uniform grid
@@ -52,6 +54,7 @@ typedef struct {
     double t_min;                    /* lower bound of the hit distance: t_min < t < |d| */
     double restitution;              /* velocity factor on contact (Alg. 2: -0.5) */
     double wind_amp, wind_dir[3], wind_udir[3], wind_freq, wind_kappa, wind_phase;
+    double pin_vel[3];               /* pinned nodes move kinematically: x += dt_s*u, v = u */
 } OcCloth;
 
 typedef struct {
@@ -506,9 +509,12 @@ int oc_step_ex(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, double
             int pinned = cl->pinned && cl->pinned[i];
             if (hits) hits[i] = 0;
             if (pinned) {
-                v[3 * i] = v[3 * i + 1] = v[3 * i + 2] = 0.0;
-                if (vph) vph[((int64_t)s * N + i) * 3] = vph[((int64_t)s * N + i) * 3 + 1] =
-                    vph[((int64_t)s * N + i) * 3 + 2] = 0.0;
+                /* kinematic pin: prescribed velocity, no force, no collision */
+                for (int k = 0; k < 3; k++) {
+                    v[3 * i + k] = cl->pin_vel[k];
+                    x[3 * i + k] += cl->dt_s * cl->pin_vel[k];
+                    if (vph) vph[((int64_t)s * N + i) * 3 + k] = cl->pin_vel[k];
+                }
                 continue;
             }
             double S[3], E[3];
@@ -735,8 +741,8 @@ int oc_step_edges(const OcCloth *cl, const OcMesh *mesh, const OcGrid *grid, dou
             const int pinned = cl->pinned && cl->pinned[i];
             for (int k = 0; k < 3; k++) {
                 if (pinned) {
-                    v[3 * i + k] = 0.0;
-                    E[3 * i + k] = x[3 * i + k];
+                    v[3 * i + k] = cl->pin_vel[k];
+                    E[3 * i + k] = x[3 * i + k] + cl->dt_s * cl->pin_vel[k];
                 } else {
                     v[3 * i + k] += cl->dt_s * A[3 * i + k];
                     E[3 * i + k] = x[3 * i + k] + cl->dt_s * v[3 * i + k];

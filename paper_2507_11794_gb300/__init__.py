@@ -55,6 +55,8 @@ def make_desc(p, keep: list, flags: int = 0) -> capi.ClothDesc:
     d.mt_t_min, d.restitution = p.mt_t_min, p.restitution
     d.wind.amp, d.wind.freq, d.wind.kappa, d.wind.phase = p.wind.amp, p.wind.freq, p.wind.kappa, p.wind.phase
     d.flags = int(flags)
+    for k in range(3):
+        d.pin_velocity[k] = float(getattr(p, "pin_velocity", (0.0, 0.0, 0.0))[k])
     N = d.nx * d.ny
 
     def fbuf(a, n):

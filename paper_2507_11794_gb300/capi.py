@@ -69,6 +69,7 @@ class ClothDesc(C.Structure):
         ("restitution", C.c_float),
         ("wind", ClothWind),
         ("flags", C.c_uint32),
+        ("pin_velocity", C.c_float * 3),
     ]
 
 

@@ -116,6 +116,7 @@ void cloth_fill_params(ClothHandle *h)
         p.ks[a] = d.ks[a];
         p.kd[a] = d.kd[a];
         p.g[a] = d.gravity[a];
+        p.pin_vel[a] = d.pin_velocity[a];
         p.w_dir[a] = d.wind.dir[a];
     }
     // rest lengths of the six directions from the flat grid, in double
@@ -262,7 +263,7 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
     if (!finite3(d.origin) || !finite3(d.du) || !finite3(d.dv) || !finite3(d.ks) || !finite3(d.kd) ||
         !finite3(d.gravity) || !finite3(d.wind.dir) || !finite3(d.wind.udir) || !isfinite(d.wind.amp) ||
         !isfinite(d.wind.freq) || !isfinite(d.wind.kappa) || !isfinite(d.wind.phase) || !isfinite(d.contact_offset) ||
-        !isfinite(d.mt_eps) || !isfinite(d.mt_t_min) || !isfinite(d.restitution))
+        !isfinite(d.mt_eps) || !isfinite(d.mt_t_min) || !isfinite(d.restitution) || !finite3(d.pin_velocity))
         return fail(CLOTH_ERR_INVALID_ARG, "non-finite parameter in desc");
     const long long S = spring_count(d.nx, d.ny);
     if (d.init_pos)

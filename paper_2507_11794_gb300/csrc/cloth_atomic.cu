@@ -135,9 +135,9 @@ __global__ void __launch_bounds__(NODE_THREADS) node_integrate_kernel(const __gr
             }
             float wx = fmaf(p.dt, ax, vx), wy = fmaf(p.dt, ay, vy), wz = fmaf(p.dt, az, vz);
             float xx = fmaf(p.dt, wx, px), xy = fmaf(p.dt, wy, py), xz = fmaf(p.dt, wz, pz);
-            if (pinned) {
-                xx = px; xy = py; xz = pz;
-                wx = wy = wz = 0.0f;
+            if (pinned) {  // kinematic: x += dt u, v = u (u = 0: fixed)
+                xx = fmaf(p.dt, p.pin_vel[0], px); xy = fmaf(p.dt, p.pin_vel[1], py); xz = fmaf(p.dt, p.pin_vel[2], pz);
+                wx = p.pin_vel[0]; wy = p.pin_vel[1]; wz = p.pin_vel[2];
             }
             if (MESH)
                 need = !pinned && fmaxf(px, xx) >= p.mlo[0] && fminf(px, xx) <= p.mhi[0] &&

@@ -37,6 +37,7 @@ struct StepParams {
     float L0[CLOTH_NDIR];      // rest length per direction
     float inv_mass, dt;
     float g[3];
+    float pin_vel[3];          // pinned nodes: x += dt pin_vel, v = pin_vel
     // wind: phase = omega*t + phase0 + col*kc + row*kr
     int has_wind;
     float w_amp, w_dir[3];

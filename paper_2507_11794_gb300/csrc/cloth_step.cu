@@ -351,13 +351,16 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
             const float2 dt = bc(p.dt);
             float2 wx = fma2(dt, ax, P0.vx), wy = fma2(dt, ay, P0.vy), wz = fma2(dt, az, P0.vz);
             float2 xx = fma2(dt, wx, P0.px), xy = fma2(dt, wy, P0.py), xz = fma2(dt, wz, P0.pz);
+            // pinned nodes move kinematically: x += dt u, v = u (u = 0: fixed)
             if (pinA) {
-                xx.x = P0.px.x; xy.x = P0.py.x; xz.x = P0.pz.x;
-                wx.x = wy.x = wz.x = 0.0f;
+                xx.x = fmaf(p.dt, p.pin_vel[0], P0.px.x); xy.x = fmaf(p.dt, p.pin_vel[1], P0.py.x);
+                xz.x = fmaf(p.dt, p.pin_vel[2], P0.pz.x);
+                wx.x = p.pin_vel[0]; wy.x = p.pin_vel[1]; wz.x = p.pin_vel[2];
             }
             if (pinB) {
-                xx.y = P0.px.y; xy.y = P0.py.y; xz.y = P0.pz.y;
-                wx.y = wy.y = wz.y = 0.0f;
+                xx.y = fmaf(p.dt, p.pin_vel[0], P0.px.y); xy.y = fmaf(p.dt, p.pin_vel[1], P0.py.y);
+                xz.y = fmaf(p.dt, p.pin_vel[2], P0.pz.y);
+                wx.y = p.pin_vel[0]; wy.y = p.pin_vel[1]; wz.y = p.pin_vel[2];
             }
             if (MESH) {
                 // nodes whose path box reaches the box of the non-empty grid

@@ -52,7 +52,7 @@ def test_struct_layout_matches_c(capi, tmp_path):
 int main(void) {
   printf("ClothDesc %zu\nClothWind %zu\nClothInfo %zu\nClothGridParams %zu\n", sizeof(ClothDesc), sizeof(ClothWind), sizeof(ClothInfo), sizeof(ClothGridParams));
   F(ClothDesc, ks_spring); F(ClothDesc, pinned); F(ClothDesc, gravity); F(ClothDesc, dt);
-  F(ClothDesc, substeps); F(ClothDesc, mt_t_min); F(ClothDesc, wind); F(ClothDesc, flags);
+  F(ClothDesc, substeps); F(ClothDesc, mt_t_min); F(ClothDesc, wind); F(ClothDesc, flags); F(ClothDesc, pin_velocity);
   F(ClothInfo, substeps_done); F(ClothInfo, pos_planes); F(ClothInfo, vel_planes); F(ClothInfo, ntris);
   F(ClothInfo, grid_h); F(ClothInfo, grid_entries); F(ClothInfo, has_per_spring); F(ClothInfo, row_pitch);
   F(ClothGridParams, origin); F(ClothGridParams, dims); F(ClothGridParams, ncells); F(ClothGridParams, nentries);

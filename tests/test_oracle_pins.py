@@ -619,3 +619,36 @@ def test_edge_phase_does_not_see_edges_parallel_to_the_surface(oracle_lib):
     x, _, hits = oracle_lib.step_edges(oracle_lib.Cloth(sc), pos, vel, 0, 1, oracle_lib.Grid(*floor_mesh()),
                                        want_hits=True)
     assert hits.sum() == 0 and np.all(x[:, 1] < 0.0)
+
+
+# --------------------------------------------------- kinematic pins (f3)
+
+@pytest.mark.parametrize("edges", [False, True])
+def test_pinned_nodes_move_at_the_prescribed_velocity(oracle_lib, edges):
+    # a pinned node under any force moves exactly x0 + k dt_s u with v = u;
+    # its free neighbour is pulled along by the spring
+    u = (0.4, -0.1, 0.25)
+    pos = np.array([[0.2, 0.5, 0.3], [0.3, 0.5, 0.3]], np.float32)
+    pinned = np.array([1, 0], np.uint8)
+    sc = make_scene(2, 1, pos=pos, du=(0.1, 0, 0), dv=(0, 0, 0.1), ks=(50.0, 0, 0), kd=(0.1, 0, 0),
+                    total_mass=0.02, gravity=(0, -9.81, 0), dt=1e-3, substeps=4, pinned=pinned, mesh=floor_mesh())
+    sc.pin_velocity = u
+    cl = oracle_lib.Cloth(sc)
+    grid = oracle_lib.Grid(*floor_mesh())
+    f = oracle_lib.step_edges if edges else oracle_lib.step
+    k = 200
+    x, v = f(cl, pos, np.zeros_like(pos), 0, k, grid)
+    np.testing.assert_allclose(x[0], pos[0].astype(np.float64) + k * (1e-3 / 4) * np.array(u), rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(v[0], np.array(u))
+    assert x[1, 0] > pos[1, 0] + 0.005  # the free node follows (the pin moved 0.02 m)
+
+
+def test_pulling_scene_is_the_hanging_model_with_moving_pins(oracle_lib):
+    # zero pin velocity reduces the pulling scene's integrator to fixed pins
+    sc = cs.pulling_scene(12, "sphere")
+    x0 = oracle_lib.run(sc, 3)
+    sc.pin_velocity = (0.0, 0.0, 0.0)
+    x1 = oracle_lib.run(sc, 3)
+    pin = sc.pinned.astype(bool)
+    np.testing.assert_array_equal(x1[0][pin], sc.init_pos[pin].astype(np.float64))
+    np.testing.assert_allclose(x0[0][pin][:, 0] - x1[0][pin][:, 0], 3 * (1 / 1200) * 0.5, rtol=0, atol=1e-12)
