@@ -70,17 +70,29 @@ def measured_peaks():
         return None
 
 
+def code_hash(path: str) -> str:
+    """sha256 (16 hex digits) of a C/CUDA source with its comments and
+    whitespace removed: the same for edits that do not change the code."""
+    import re
+    src = open(path, encoding="utf-8").read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = re.sub(r"\s+", "", src)
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def profile_traffic():
     """Per-launch DRAM bytes of the substep kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    summary, if it was taken on the current kernel code (comment and
+    whitespace changes aside)."""
     try:
-        src_hash = hashlib.sha256(open(STEP_SRC, "rb").read()).hexdigest()[:16]
+        src_hash = code_hash(STEP_SRC)
         vals = {}
         for line in open(PROFILE_SUMMARY):
             if ":" in line:
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-        if vals.get("source_sha256_16") == src_hash and "dram_bytes_per_launch" in vals:
+        if vals.get("code_sha256_16", "").split()[:1] == [src_hash] and "dram_bytes_per_launch" in vals:
             return float(vals["dram_bytes_per_launch"])
     except (OSError, ValueError):
         pass

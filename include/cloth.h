@@ -149,7 +149,14 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out);
  * Synchronises the stream. */
 int cloth_set_mesh(ClothHandle *h, const float *verts, int32_t nverts, const int32_t *tris, int32_t ntris);
 
-/* Enqueue nsteps steps (nsteps * substeps substeps) on the stream. */
+/* Enqueue nsteps steps (nsteps * substeps substeps) on the stream.  Each
+ * substep: spring and damping forces (Algorithm 1), symplectic Euler with
+ * gravity, wind and pins (Section 3), then, with a surface model, the grid
+ * broad phase, the extended Moller-Trumbore narrow phase and the averaged
+ * response (Algorithm 2).  Replayed from a CUDA graph of one step unless
+ * CLOTH_FLAG_NO_GRAPH.  Errors: CLOTH_ERR_INVALID_ARG (nsteps < 0),
+ * CLOTH_ERR_CUDA; device-side flags are reported by the next cloth_sync or
+ * cloth_read. */
 int cloth_step(ClothHandle *h, int32_t nsteps);
 
 /* Copy the current state to caller-owned host [N][3] arrays (either may be

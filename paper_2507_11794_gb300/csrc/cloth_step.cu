@@ -496,8 +496,9 @@ __global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) substep_k
 }
 
 // Second kernel of a substep with a surface model: broad + narrow phase and
-// response of every node the walk marked (one thread per node), then the
-// substep counter advances.
+// response of every node the walk listed (warp-cooperative, collide_list),
+// then the substep counter advances.
+
 // List entries of one cloth.
 struct OneClothList {
     const StepParams &p;
