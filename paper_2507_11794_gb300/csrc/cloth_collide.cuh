@@ -146,7 +146,7 @@ __device__ __forceinline__ bool collide_t(const StepParams &p, float sx, float s
 //  3. owner lanes apply the response.
 // A path whose box spans more than COLL_MAXC cells (a node moving further
 // than a cell in one substep) is handled by its own lane with collide_t.
-constexpr int COLL_WARPS = 4;  // warps per CTA of the collision kernels
+constexpr int COLL_WARPS = 8;  // warps per CTA of the collision kernels
 constexpr int COLL_MAXC = 8;   // cells of a box spread over the warp
 
 struct CollLane {

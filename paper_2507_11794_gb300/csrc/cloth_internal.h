@@ -68,7 +68,7 @@ struct StepParams {
 
 // CTAs per SM of the collision kernels (grid = SMs x this).
 #ifndef CLOTH_COLL_CTAS_PER_SM
-#define CLOTH_COLL_CTAS_PER_SM 4
+#define CLOTH_COLL_CTAS_PER_SM 2
 #endif
 
 // Launch one substep (reads state k&1, writes the other, advances ctrl->k).

@@ -38,7 +38,7 @@ namespace {
 #define CLOTH_WALK_UNROLL 1
 #endif
 #ifndef CLOTH_COLL_MINB
-#define CLOTH_COLL_MINB 4
+#define CLOTH_COLL_MINB 2
 #endif
 #define CLOTH_PRAGMA(x) _Pragma(#x)
 #define CLOTH_UNROLL(n) CLOTH_PRAGMA(unroll n)
