@@ -114,17 +114,27 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
+                                          "-i", str(self.gpu), "-lms", "20"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi takes a while to start: wait for its first sample so the
+            # timed region is covered
+            t_end = time.perf_counter() + 5.0
+            while not self.rows and time.perf_counter() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except OSError:
             self.proc = None
+        self.window = None
         return self
+
+    def mark(self, t0: float, t1: float):
+        """The timed region, in time.perf_counter() seconds."""
+        self.window = (t0, t1)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append([x.strip() for x in line.split(",")] + [time.perf_counter()])
 
     def __exit__(self, *exc):
         if self.proc:
@@ -135,11 +145,19 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        """Median SM clock, max clock and active slowdown reasons over the
+        samples taken inside the marked timed region (plus the sample either
+        side of it, which brackets a region shorter than the sampling period)."""
+        rows = [r for r in self.rows if len(r) >= 10]
+        if self.window is not None and rows:
+            t0, t1 = self.window
+            inside = [i for i, r in enumerate(rows) if t0 <= r[-1] <= t1]
+            before = [i for i, r in enumerate(rows) if r[-1] < t0][-1:]
+            after = [i for i, r in enumerate(rows) if r[-1] > t1][:1]
+            rows = [rows[i] for i in before + inside + after]
         mhz, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            if len(r) < 9:
-                continue
+        for r in rows:
             try:
                 mhz.append(float(r[1]))
                 mx = float(r[2])
@@ -479,6 +497,7 @@ def run_ours(args):
             ends[i].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        clocks.mark(wall0, wall0 + wall)
     barrier(pg)
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     pos, vel = cl.read()
