@@ -65,7 +65,9 @@ enum {
  * The force law, integrator and collision phase are those of the default
  * path, but the order of the additions, and so the last bits of the state,
  * vary from run to run.  Kept as an A/B of the paper's design against the
- * default fused column walk.  Not accepted by cloth_batch_create. */
+ * default fused column walk.  Not accepted by cloth_batch_create or
+ * cloth_rollout_create (the adjoint recomputes segments and needs bitwise
+ * reproducible forward states). */
 #define CLOTH_FLAG_ATOMIC_SPRINGS 2u
 /* The paper's own narrow phase instead of the node-path test: the edges of
  * the cloth triangles (the grid's quads split along their (r,c)-(r+1,c+1)
@@ -293,7 +295,10 @@ typedef struct ClothRollout ClothRollout;
 
 /* The cloth's current state (at its current substep count) becomes the
  * rollout's initial state.  A cloth created without per-spring constants gets
- * per-spring planes filled from its per-type constants. */
+ * per-spring planes filled from its per-type constants.  Errors:
+ * CLOTH_ERR_INVALID_ARG (NULL, nsteps or checkpoint_every < 1, a cloth created
+ * with CLOTH_FLAG_ATOMIC_SPRINGS or CLOTH_FLAG_EDGE_COLLISION), CLOTH_ERR_OOM,
+ * CLOTH_ERR_CUDA. */
 int cloth_rollout_create(ClothHandle *h, int32_t nsteps, int32_t checkpoint_every, ClothRollout **out);
 /* Forward pass from the initial state: d_ks, d_kd (S floats, canonical
  * order; NULL keeps the current constants), d_v0 ([N][3] initial velocities;

@@ -254,8 +254,12 @@ int cloth_rollout_create(ClothHandle *h, int32_t nsteps, int32_t checkpoint_ever
     if (!h) return rfail(CLOTH_ERR_INVALID_ARG, "null handle");
     if (h->dead) return rfail(CLOTH_ERR_STATE, "handle unusable after an earlier CUDA error");
     if (nsteps < 1 || checkpoint_every < 1) return rfail(CLOTH_ERR_INVALID_ARG, "nsteps and checkpoint_every >= 1");
-    if (h->desc.flags & CLOTH_FLAG_EDGE_COLLISION)
-        return rfail(CLOTH_ERR_INVALID_ARG, "the adjoint covers the node-path narrow phase, not CLOTH_FLAG_EDGE_COLLISION");
+    // the reverse pass recomputes each segment and must see the forward pass's
+    // exact states (the atomic path is not bitwise reproducible) and its
+    // node-path contacts
+    if (h->desc.flags & (CLOTH_FLAG_EDGE_COLLISION | CLOTH_FLAG_ATOMIC_SPRINGS))
+        return rfail(CLOTH_ERR_INVALID_ARG,
+                     "rollouts need the default path (no CLOTH_FLAG_EDGE_COLLISION or CLOTH_FLAG_ATOMIC_SPRINGS)");
     const ClothDesc &d = h->desc;
     const long long N = h->n, st = h->stride;
     ClothRollout *ro = new (std::nothrow) ClothRollout();

@@ -78,3 +78,12 @@ def test_atomic_path_profiles_and_rollout_forward(cloth_lib):
         b.step(2)
         assert w > 0 and c > 0
         assert max_err(a.read()[0], b.read()[0]) <= 1e-5
+
+
+def test_atomic_path_is_rejected_by_the_rollout(cloth_lib):
+    import ctypes as C
+    sc = cs.small_collision_scene(n=12, level=2, gap=0.01)
+    with cloth_lib.Cloth(sc, flags=_atomic(cloth_lib)) as cl:
+        ro = C.c_void_p()
+        rc = cloth_lib.capi.lib().cloth_rollout_create(C.c_void_p(cl.h), 4, 2, C.byref(ro))
+        assert rc == cloth_lib.capi.CLOTH_ERR_INVALID_ARG
