@@ -170,12 +170,10 @@ __global__ void __launch_bounds__(NODE_THREADS) node_integrate_kernel(const __gr
     if (MESH) return;  // the collision kernel finishes the substep
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         const unsigned prev = atomicAdd(&p.ctrl->blocks_done, 1u);
         if (prev == gridDim.x - 1) {
             p.ctrl->blocks_done = 0;
             p.ctrl->k = k + 1;
-            __threadfence();
         }
     }
 }

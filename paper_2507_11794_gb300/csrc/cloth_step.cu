@@ -53,6 +53,13 @@ constexpr unsigned FULL = 0xffffffffu;
 #ifndef CLOTH_PDL
 #define CLOTH_PDL 1
 #endif
+// Substep completion: the last CTA of the kernel that ends a substep (found by
+// an atomic count of finished CTAs) advances the substep counter and resets
+// the per-substep counters.  It reads nothing the other CTAs wrote, and every
+// CTA has read those control words before its increment; the next kernel
+// reads them only after this one has completed (or after griddepcontrol.wait),
+// which makes all writes visible.  So no memory fence is taken: a fence would
+// make each CTA wait for its own stores to drain, about 1 us per launch.
 __device__ __forceinline__ void pdl_wait()
 {
 #if CLOTH_PDL
@@ -485,12 +492,10 @@ __global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) substep_k
     __syncthreads();
     if (threadIdx.x == 0) {
         // the last CTA to finish advances the substep counter for the next launch
-        __threadfence();
         const unsigned prev = atomicAdd(&p.ctrl->blocks_done, 1u);
         if (prev == gridDim.x - 1) {
             p.ctrl->blocks_done = 0;
             p.ctrl->k = k + 1;
-            __threadfence();
         }
     }
 }
@@ -531,13 +536,11 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kern
         atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         const unsigned prev = atomicAdd(&p.ctrl->blocks_done, 1u);
         if (prev == gridDim.x - 1) {
             p.ctrl->blocks_done = 0;
             *p.coll_count = 0u;
             p.ctrl->k = k + 1;
-            __threadfence();
         }
     }
 }
@@ -592,13 +595,11 @@ __global__ void __launch_bounds__(256) edge_apply_kernel(const __grid_constant__
     __syncthreads();
     if (threadIdx.x == 0) {
         // the last CTA resets the list and advances the substep counter
-        __threadfence();
         const unsigned prev = atomicAdd(&p.ctrl->blocks_done, 1u);
         if (prev == gridDim.x - 1) {
             p.ctrl->blocks_done = 0;
             *p.coll_count = 0u;
             p.ctrl->k = k + 1;
-            __threadfence();
         }
     }
 }
@@ -648,12 +649,10 @@ __global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) batch_sub
     __syncthreads();
     if (threadIdx.x == 0) {
         // the last CTA re-arms the work counter (the collision kernel advances k)
-        __threadfence();
         const unsigned prev = atomicAdd(&b.ctrl->blocks_done, 1u);
         if (prev == gridDim.x - 1) {
             b.ctrl->blocks_done = 0;
             *b.work = 0u;
-            __threadfence();
         }
     }
 }
@@ -689,13 +688,11 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) batch_collid
         atomicOr(&b.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         const unsigned prev = atomicAdd(&b.ctrl->blocks_done, 1u);
         if (prev == gridDim.x - 1) {
             b.ctrl->blocks_done = 0;
             *b.coll_count = 0u;
             b.ctrl->k = k + 1;
-            __threadfence();
         }
     }
 }
