@@ -298,3 +298,23 @@ def test_penetration_bounded_gpu_config1(cloth_lib):
             if inside.any():
                 depth = -np.max(p[inside].astype(np.float64) @ n.T - off[None, :], axis=1)
                 assert np.all(depth <= 1e-2), depth
+
+
+@pytest.mark.parametrize("mode", ["atomic", "edges"])
+def test_minimal_cloths_in_the_alternative_paths(cloth_lib, oracle_lib, mode):
+    # ragged and degenerate grids through the atomic spring path and the edge
+    # narrow phase: the same tolerances as the default path (edge mode against
+    # the oracle's edge reading)
+    flag = {"atomic": cloth_lib.capi.CLOTH_FLAG_ATOMIC_SPRINGS, "edges": cloth_lib.capi.CLOTH_FLAG_EDGE_COLLISION}[mode]
+    for nx, ny in [(1, 1), (1, 2), (2, 1), (3, 1), (1, 5), (2, 2), (5, 3), (61, 2)]:
+        sc = make_scene(nx, ny, ks=(50.0, 20.0, 10.0), kd=(0.1, 0.1, 0.1), gravity=(0, -9.81, 0), dt=1e-3,
+                        substeps=2, mesh=floor_mesh(), origin=(0.3, 0.012, 0.3), du=(0.007, 0, 0),
+                        dv=(0, 0.004, 0.005))
+        p, v = run_gpu(cloth_lib, sc, 1, flags=flag)
+        if mode == "edges":
+            cl = oracle_lib.Cloth(sc)
+            x, _ = oracle_lib.step_edges(cl, sc.init_pos, sc.init_vel, 0, sc.substeps,
+                                         oracle_lib.Grid(sc.mesh_verts, sc.mesh_tris))
+        else:
+            x, _ = run_oracle(oracle_lib, sc, 1)
+        assert np.all(np.isfinite(p)) and max_err(p, x) <= TOL_1, (nx, ny)
