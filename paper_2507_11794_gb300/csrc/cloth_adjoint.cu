@@ -18,10 +18,19 @@
 #include <new>
 #include <vector>
 
-#include "cloth_collide.cuh"
 #include "cloth_internal.h"
 
 namespace {
+
+// The reverse kernels are launched with programmatic stream serialisation:
+// a launch may start while its predecessor drains, and griddepcontrol.wait,
+// before any global memory access, blocks until the predecessor has
+// completed and its writes are visible.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 
 // Canonical spring directions (drow, dcol).
 constexpr int DR[CLOTH_NDIR] = {0, 1, 1, 1, 0, 2};
@@ -29,21 +38,20 @@ constexpr int DC[CLOTH_NDIR] = {1, 0, 1, -1, 2, 0};
 __device__ __forceinline__ int dev_dr(int d) { return d == 0 || d == 4 ? 0 : (d == 5 ? 2 : 1); }
 __device__ __forceinline__ int dev_dc(int d) { return d == 0 ? 1 : (d == 1 || d == 5 ? 0 : (d == 2 ? 1 : (d == 3 ? -1 : 2))); }
 
-// Reverse of the response and the Euler update of one substep, one thread
-// per node.  xs: 6 planes (x, v at the substep's start), vs: 3 planes (v*),
-// lx/lv: adjoints of the substep's end; outputs lS (x part), lvp (v* part)
-// and lF = dt/m lvp (force adjoint; 0 for pinned nodes).
-__global__ void adj_contact_kernel(const StepParams p, const float *__restrict__ xs, const float *__restrict__ vs,
-                                   const float *__restrict__ lx, const float *__restrict__ lv, float *__restrict__ lS,
-                                   float *__restrict__ lvp, float *__restrict__ lF)
+// Reverse of the response and the Euler update of one substep at node o.
+// xs: 6 planes (x, v at the substep's start), vs: 3 planes (v*), cd / cb:
+// the response data the recompute's collision pass recorded for the nodes
+// that hit (m, r, g1 / K, g2 / K; see coll_record) and their bits; l, m:
+// adjoints of the node's end position and velocity; writes lS (x part), lvp
+// (v* part) and lF = dt/m lvp (force adjoint; 0 for a pinned node).
+__device__ __forceinline__ void contact_adj(const StepParams &p, const float *__restrict__ xs,
+                                            const float *__restrict__ vs, const float *__restrict__ cd,
+                                            const uint32_t *__restrict__ cb, long long o, const float l[3],
+                                            const float mv[3], float *__restrict__ lS, float *__restrict__ lvp,
+                                            float *__restrict__ lF)
 {
     const long long st = p.stride;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)p.ny * p.pitch) return;
-    const int c = (int)(idx % p.pitch);
-    if (c >= p.nx) return;
-    const long long o = idx;
-    const float l0 = lx[o], l1 = lx[st + o], l2 = lx[2 * st + o];
+    const float l0 = l[0], l1 = l[1], l2 = l[2];
     const bool pinned = p.pin_bits && ((p.pin_bits[o >> 5] >> (o & 31)) & 1u);
     if (pinned) {
         lS[o] = l0; lS[st + o] = l1; lS[2 * st + o] = l2;
@@ -51,29 +59,26 @@ __global__ void adj_contact_kernel(const StepParams p, const float *__restrict__
         lF[o] = lF[st + o] = lF[2 * st + o] = 0.0f;
         return;
     }
-    const float m0 = lv[o], m1 = lv[st + o], m2 = lv[2 * st + o];
-    const float sx = xs[o], sy = xs[st + o], sz = xs[2 * st + o];
-    const float wx = vs[o], wy = vs[st + o], wz = vs[2 * st + o];
-    // the predicted end exactly as the forward pass formed it
-    const float ex = fmaf(p.dt, wx, sx), ey = fmaf(p.dt, wy, sy), ez = fmaf(p.dt, wz, sz);
+    const float m0 = mv[0], m1 = mv[1], m2 = mv[2];
     float s0 = l0, s1 = l1, s2 = l2;
     float q0 = fmaf(p.dt, l0, m0), q1 = fmaf(p.dt, l1, m1), q2 = fmaf(p.dt, l2, m2);
-    if (p.has_mesh) {
-        float ox, oy, oz, g1[3] = {0.0f, 0.0f, 0.0f}, g2[3] = {0.0f, 0.0f, 0.0f}, mK[5];
-        if (collide_t<true>(p, sx, sy, sz, ex, ey, ez, ox, oy, oz, g1, g2, mK)) {
-            const float m = mK[0], invK = 1.0f / mK[1], rx = mK[2], ry = mK[3], rz = mK[4];
-            const float rl = rx * l0 + ry * l1 + rz * l2;
-            s0 = l0 + g1[0] * invK * rl;
-            s1 = l1 + g1[1] * invK * rl;
-            s2 = l2 + g1[2] * invK * rl;
-            const float r0 = m * l0 + g2[0] * invK * rl, r1 = m * l1 + g2[1] * invK * rl,
-                        r2 = m * l2 + g2[2] * invK * rl;
-            const float rr = rx * r0 + ry * r1 + rz * r2;
-            const float inv_nv = rsqrtf(wx * wx + wy * wy + wz * wz);
-            q0 = (r0 - rx * rr) * inv_nv + p.restitution * m0;
-            q1 = (r1 - ry * rr) * inv_nv + p.restitution * m1;
-            q2 = (r2 - rz * rr) * inv_nv + p.restitution * m2;
-        }
+    if (cb && ((cb[o >> 5] >> (o & 31)) & 1u)) {
+        // x' = S + m r with r = v*/|v*|, v' = c v*: dx'/dS = I + r g1^T / K,
+        // dx'/dr = m I + r g2^T / K (t_k of the active hits vary with S and r)
+        const float wx = vs[o], wy = vs[st + o], wz = vs[2 * st + o];
+        const float m = cd[o], rx = cd[st + o], ry = cd[2 * st + o], rz = cd[3 * st + o];
+        const float a0 = cd[4 * st + o], a1 = cd[5 * st + o], a2 = cd[6 * st + o];
+        const float b0 = cd[7 * st + o], b1 = cd[8 * st + o], b2 = cd[9 * st + o];
+        const float rl = rx * l0 + ry * l1 + rz * l2;
+        s0 = l0 + a0 * rl;
+        s1 = l1 + a1 * rl;
+        s2 = l2 + a2 * rl;
+        const float r0 = m * l0 + b0 * rl, r1 = m * l1 + b1 * rl, r2 = m * l2 + b2 * rl;
+        const float rr = rx * r0 + ry * r1 + rz * r2;
+        const float inv_nv = rsqrtf(wx * wx + wy * wy + wz * wz);
+        q0 = (r0 - rx * rr) * inv_nv + p.restitution * m0;
+        q1 = (r1 - ry * rr) * inv_nv + p.restitution * m1;
+        q2 = (r2 - rz * rr) * inv_nv + p.restitution * m2;
     }
     lS[o] = s0; lS[st + o] = s1; lS[2 * st + o] = s2;
     lvp[o] = q0; lvp[st + o] = q1; lvp[2 * st + o] = q2;
@@ -110,59 +115,134 @@ __device__ __forceinline__ void spring_adj(const float *xo, const float *vo, con
     gkd = um * ud;
 }
 
-// Reverse of the spring forces, one thread per node: the node's adjoints of
-// the substep's start state (lx, lv) and += gradients of the springs it owns.
-__global__ void adj_spring_kernel(const StepParams p, const float *__restrict__ xs, const float *__restrict__ lF,
-                                  const float *__restrict__ lS, const float *__restrict__ lvp, float *__restrict__ lx,
-                                  float *__restrict__ lv, double *__restrict__ gks, double *__restrict__ gkd)
+// Reverse of the spring forces of one substep at node (r, c), offset o:
+// xs the substep's start state, lF its force adjoints (all nodes), lS / lvp
+// the node's own adjoint parts; returns the adjoints of the node's start
+// position (gx) and velocity (gv) and adds the gradients of the springs the
+// node owns.
+__device__ __forceinline__ void spring_adj_node(const StepParams &p, const float *__restrict__ xs,
+                                                const float *__restrict__ lF, const float *__restrict__ lS,
+                                                const float *__restrict__ lvp, long long o, int r, int c,
+                                                double *__restrict__ gks, double *__restrict__ gkd, float gx[3],
+                                                float gv[3])
 {
+    const long long st = p.stride;
+    const float xi[3] = {xs[o], xs[st + o], xs[2 * st + o]};
+    const float vi[3] = {xs[3 * st + o], xs[4 * st + o], xs[5 * st + o]};
+    const float fi[3] = {lF[o], lF[st + o], lF[2 * st + o]};
+    gx[0] = lS[o]; gx[1] = lS[st + o]; gx[2] = lS[2 * st + o];
+    gv[0] = lvp[o]; gv[1] = lvp[st + o]; gv[2] = lvp[2 * st + o];
+    // Gather first, compute after: every load is issued unconditionally (a
+    // missing neighbour reads the node itself) so that the twelve springs'
+    // loads are all in flight together; a missing spring's terms are
+    // discarded by the validity selects.  Spring t < 6: owned, direction t;
+    // t >= 6: incoming along direction t - 6.
+    float xn[12][3], vn[12][3], ln[12][3], ksn[12], kdn[12];
+    double sk[CLOTH_NDIR], sd[CLOTH_NDIR];
+    bool ok[12];
+#pragma unroll
+    for (int t = 0; t < 12; t++) {
+        const int d = t < 6 ? t : t - 6;
+        const int r2 = t < 6 ? r + dev_dr(d) : r - dev_dr(d);
+        const int c2 = t < 6 ? c + dev_dc(d) : c - dev_dc(d);
+        ok[t] = r2 >= 0 && r2 < p.ny && c2 >= 0 && c2 < p.nx;
+        const long long e = ok[t] ? (long long)r2 * p.pitch + c2 : o;
+        xn[t][0] = xs[e]; xn[t][1] = xs[st + e]; xn[t][2] = xs[2 * st + e];
+        vn[t][0] = xs[3 * st + e]; vn[t][1] = xs[4 * st + e]; vn[t][2] = xs[5 * st + e];
+        ln[t][0] = lF[e]; ln[t][1] = lF[st + e]; ln[t][2] = lF[2 * st + e];
+        const long long so = d * st + (t < 6 ? o : e);  // the spring's slot: its owner's offset
+        ksn[t] = p.ks_slot[so];
+        kdn[t] = p.kd_slot[so];
+        if (t < 6) {
+            sk[d] = gks[so];
+            sd[d] = gkd[so];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 12; u++) {
+        // the order of the sums: owned d, incoming d, owned d + 1, ...
+        const int d = u >> 1, t = (u & 1) ? d + 6 : d;
+        float a[3], b[3], g1, g2;
+        if (t < 6) {
+            const float mu[3] = {fi[0] - ln[t][0], fi[1] - ln[t][1], fi[2] - ln[t][2]};
+            spring_adj(xi, vi, xn[t], vn[t], mu, ksn[t], kdn[t], p.L0[d], a, b, g1, g2);
+            if (ok[t]) {
+                gx[0] -= a[0]; gx[1] -= a[1]; gx[2] -= a[2];
+                gv[0] -= b[0]; gv[1] -= b[1]; gv[2] -= b[2];
+                // per-spring sums over the substeps in double: FP64 only in these reductions
+                gks[d * st + o] = sk[d] + (double)g1;
+                gkd[d * st + o] = sd[d] + (double)g2;
+            }
+        } else {
+            const float mu[3] = {ln[t][0] - fi[0], ln[t][1] - fi[1], ln[t][2] - fi[2]};
+            spring_adj(xn[t], vn[t], xi, vi, mu, ksn[t], kdn[t], p.L0[d], a, b, g1, g2);
+            if (ok[t]) {
+                gx[0] += a[0]; gx[1] += a[1]; gx[2] += a[2];
+                gv[0] += b[0]; gv[1] += b[1]; gv[2] += b[2];
+            }
+        }
+    }
+}
+
+// Buffers of one reverse launch (plane layout, stride p.stride).
+struct AdjArgs {
+    const float *xs_s;      // spring part: start state of substep j (6 planes)
+    const float *lF_s;      // spring part: force adjoints of substep j
+    const float *xs_c;      // contact part: start state of the substep it reverses (6 planes)
+    const float *vs_c;      // contact part: that substep's v* (3 planes)
+    const float *cd_c;      // contact part: that substep's recorded response data (10 planes)
+    const uint32_t *cb_c;   // contact part: its hit bits (null without a mesh)
+    float *lF_c;            // contact part: its force adjoints (never lF_s: neighbours read lF_s)
+    float *lS, *lvp;        // the node's own parts: read by the spring part, then written by the contact part
+    float *lx, *lv;         // contact only: the end-state adjoints read; spring only: start-state adjoints written
+    double *gks, *gkd;      // per-spring gradient sums
+};
+
+// One reverse launch, one thread per node.  SPRING: the spring reverse of
+// substep j gives the node's start-state adjoints; CONTACT: the response and
+// Euler reverse of the substep before (of the substep given, without
+// SPRING) consumes them at once.  Reversing a segment of n substeps takes
+// n + 1 launches: contact(n-1), then spring(j) + contact(j-1) for
+// j = n-1..1, then spring(0).
+constexpr int ADJ_THREADS = 128;
+template <bool SPRING, bool CONTACT>
+__global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(const StepParams p, const AdjArgs a)
+{
+    pdl_enter();
     const long long st = p.stride;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)p.ny * p.pitch) return;
     const int r = (int)(idx / p.pitch), c = (int)(idx % p.pitch);
     if (c >= p.nx) return;
     const long long o = idx;
-    const float xi[3] = {xs[o], xs[st + o], xs[2 * st + o]};
-    const float vi[3] = {xs[3 * st + o], xs[4 * st + o], xs[5 * st + o]};
-    const float fi[3] = {lF[o], lF[st + o], lF[2 * st + o]};
-    float gx[3] = {lS[o], lS[st + o], lS[2 * st + o]};
-    float gv[3] = {lvp[o], lvp[st + o], lvp[2 * st + o]};
-#pragma unroll
-    for (int d = 0; d < CLOTH_NDIR; d++) {
-        // spring owned by this node
-        {
-            const int r2 = r + dev_dr(d), c2 = c + dev_dc(d);
-            if (r2 < p.ny && c2 >= 0 && c2 < p.nx) {
-                const long long e = (long long)r2 * p.pitch + c2;
-                const float xe[3] = {xs[e], xs[st + e], xs[2 * st + e]};
-                const float ve[3] = {xs[3 * st + e], xs[4 * st + e], xs[5 * st + e]};
-                const float mu[3] = {fi[0] - lF[e], fi[1] - lF[st + e], fi[2] - lF[2 * st + e]};
-                float a[3], b[3], g1, g2;
-                spring_adj(xi, vi, xe, ve, mu, p.ks_slot[d * st + o], p.kd_slot[d * st + o], p.L0[d], a, b, g1, g2);
-                gx[0] -= a[0]; gx[1] -= a[1]; gx[2] -= a[2];
-                gv[0] -= b[0]; gv[1] -= b[1]; gv[2] -= b[2];
-                // per-spring sums over the substeps in double: FP64 only in these reductions
-                gks[d * st + o] += (double)g1;
-                gkd[d * st + o] += (double)g2;
-            }
-        }
-        // spring owned by the node at (-dr, -dc), ending here
-        {
-            const int r2 = r - dev_dr(d), c2 = c - dev_dc(d);
-            if (r2 >= 0 && c2 >= 0 && c2 < p.nx) {
-                const long long w = (long long)r2 * p.pitch + c2;
-                const float xw[3] = {xs[w], xs[st + w], xs[2 * st + w]};
-                const float vw[3] = {xs[3 * st + w], xs[4 * st + w], xs[5 * st + w]};
-                const float mu[3] = {lF[w] - fi[0], lF[st + w] - fi[1], lF[2 * st + w] - fi[2]};
-                float a[3], b[3], g1, g2;
-                spring_adj(xw, vw, xi, vi, mu, p.ks_slot[d * st + w], p.kd_slot[d * st + w], p.L0[d], a, b, g1, g2);
-                gx[0] += a[0]; gx[1] += a[1]; gx[2] += a[2];
-                gv[0] += b[0]; gv[1] += b[1]; gv[2] += b[2];
-            }
-        }
+    float l[3], m[3];
+    if (SPRING) {
+        spring_adj_node(p, a.xs_s, a.lF_s, a.lS, a.lvp, o, r, c, a.gks, a.gkd, l, m);
+    } else {
+        l[0] = a.lx[o]; l[1] = a.lx[st + o]; l[2] = a.lx[2 * st + o];
+        m[0] = a.lv[o]; m[1] = a.lv[st + o]; m[2] = a.lv[2 * st + o];
     }
-    lx[o] = gx[0]; lx[st + o] = gx[1]; lx[2 * st + o] = gx[2];
-    lv[o] = gv[0]; lv[st + o] = gv[1]; lv[2 * st + o] = gv[2];
+    if (CONTACT) {
+        contact_adj(p, a.xs_c, a.vs_c, a.cd_c, a.cb_c, o, l, m, a.lS, a.lvp, a.lF_c);
+    } else {
+        a.lx[o] = l[0]; a.lx[st + o] = l[1]; a.lx[2 * st + o] = l[2];
+        a.lv[o] = m[0]; a.lv[st + o] = m[1]; a.lv[2 * st + o] = m[2];
+    }
+}
+
+// n floats (a multiple of 4, 16-byte aligned ends) from src to dst.
+__global__ void copy_planes_kernel(const float4 *__restrict__ src, float4 *__restrict__ dst, long long n4)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+// Start of a segment's recompute: the substep counter, and the hit bits of
+// all its substeps cleared.
+__global__ void segment_begin_kernel(DevCtrl *ctrl, unsigned long long k, uint32_t *bits, long long nwords)
+{
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0) ctrl->k = k;
+    for (long long i = i0; i < nwords; i += (long long)gridDim.x * blockDim.x) bits[i] = 0u;
 }
 
 // Canonical spring order <-> [direction][r*pitch + c] slots.
@@ -202,6 +282,9 @@ __global__ void planes_aos_kernel(const float *__restrict__ planes, int n, int n
 
 inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
+// Planes of one recompute slot: x, v (3 + 3), v* (3), response data (10).
+constexpr int SLOT_PLANES = 19;
+
 }  // namespace
 
 struct ClothRollout {
@@ -211,12 +294,17 @@ struct ClothRollout {
     std::vector<unsigned long long> kseg;  // substep counter at each checkpoint (host copies for async uploads)
     float *x0 = nullptr, *v0 = nullptr;    // initial state, AoS [N][3]
     float *ckpt = nullptr;                 // nseg x 6 planes
-    float *seg = nullptr;                  // every*substeps x 9 planes (x, v, v*)
-    float *lam = nullptr;                  // lx, lv, lS, lvp, lF: 15 planes
+    float *seg = nullptr;                  // every*substeps+1 slots x 19 planes (x, v, v*, response data)
+    uint32_t *cbits = nullptr;             // every*substeps+1 slots x stride/32 hit-bit words
+    float *lam = nullptr;                  // lx, lv, lS, lvp, lF (two buffers): 18 planes
     double *gslot = nullptr;               // gks, gkd: 12 planes (double sums over substeps)
     float *final_state = nullptr;          // 6 planes
     int *map = nullptr;                    // canonical spring -> slot
     bool forward_done = false;
+    // the forward chain and the reverse pass as CUDA graphs (captured on first
+    // use; rebuilt when the cloth's kernel parameters change)
+    cudaGraphExec_t fwd_graph = nullptr, bwd_graph = nullptr;
+    unsigned long long fwd_gen = 0, bwd_gen = 0;
 };
 
 namespace {
@@ -242,6 +330,171 @@ int rfail(int code, const char *fmt, ...)
     } while (0)
 
 float *cur_state(ClothHandle *h, unsigned long long k) { return h->state + ((k & 1ull) ? 6 * h->stride : 0); }
+
+int seg_steps(const ClothRollout *ro, int g) { return (g == ro->nseg - 1) ? ro->nsteps - g * ro->every : ro->every; }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), int blocks, cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3((unsigned)ADJ_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
+
+cudaError_t copy_planes(const float *src, float *dst, long long nfloats, cudaStream_t s)
+{
+    const long long n4 = nfloats / 4;
+    const long long b = (n4 + 255) / 256;
+    copy_planes_kernel<<<(int)(b < 1 ? 1 : (b > 4096 ? 4096 : b)), 256, 0, s>>>((const float4 *)src, (float4 *)dst,
+                                                                                  n4);
+    return cudaGetLastError();
+}
+
+// The forward chain from the restored initial state: a checkpoint before
+// every segment, the segment's substeps (the cloth's own launches), and a
+// copy of the final state.
+cudaError_t enqueue_forward(ClothRollout *ro, cudaStream_t s)
+{
+    ClothHandle *h = ro->h;
+    const long long st = h->stride;
+    cudaError_t e = cudaSuccess;
+    for (int g = 0; g < ro->nseg && e == cudaSuccess; g++) {
+        e = copy_planes(cur_state(h, ro->kseg[g]), ro->ckpt + (size_t)g * 6 * st, 6 * st, s);
+        const int n = seg_steps(ro, g) * h->desc.substeps;
+        for (int q = 0; q < n && e == cudaSuccess; q++) e = launch_substep(h->params, s);
+    }
+    if (e == cudaSuccess) e = copy_planes(cur_state(h, ro->k_final), ro->final_state, 6 * st, s);
+    return e;
+}
+
+// The reverse pass over all segments, last first.  Each segment is
+// recomputed from its checkpoint with the substep kernels redirected:
+// substep j reads slot j (the checkpoint for j = 0) and writes slot j + 1 and
+// its post-integration velocity into slot j, so every substep's start state
+// stays in place without copies; the state buffers of the cloth are not
+// touched.  The reverse launches then walk the slots backwards, the force
+// adjoints of consecutive substeps alternating between two buffers.
+cudaError_t enqueue_backward(ClothRollout *ro, cudaStream_t s)
+{
+    ClothHandle *h = ro->h;
+    const long long st = h->stride;
+    const int sub = h->desc.substeps;
+    float *lF2[2] = {ro->lam + 12 * st, ro->lam + 15 * st};
+    const int blocks = nblk((long long)h->desc.ny * h->pitch, ADJ_THREADS);
+    const StepParams &p = h->params;
+    cudaError_t e = cudaSuccess;
+    for (int g = ro->nseg - 1; g >= 0 && e == cudaSuccess; g--) {
+        const int nsub = seg_steps(ro, g) * sub;
+        const unsigned long long kg = ro->kseg[g];
+        const float *ck = ro->ckpt + (size_t)g * 6 * st;
+        auto slot = [&](int j) { return ro->seg + (size_t)j * SLOT_PLANES * st; };
+        auto xstart = [&](int j) { return j == 0 ? ck : (const float *)slot(j); };
+        auto bits = [&](int j) { return ro->cbits + (size_t)j * (st / 32); };
+        const long long nwords = (long long)nsub * (st / 32);
+        const int zb = nblk(nwords, 256);
+        segment_begin_kernel<<<zb < 1 ? 1 : (zb > 1024 ? 1024 : zb), 256, 0, s>>>(h->ctrl, kg, ro->cbits, nwords);
+        e = cudaGetLastError();
+        for (int j = 0; j < nsub && e == cudaSuccess; j++) {
+            StepParams q = p;
+            float *in = const_cast<float *>(xstart(j));
+            float *out = slot(j + 1);
+            // the kernels read (k odd ? state1 : state0) and write the other
+            if ((kg + (unsigned long long)j) & 1ull) {
+                q.state1 = in;
+                q.state0 = out;
+            } else {
+                q.state0 = in;
+                q.state1 = out;
+            }
+            q.vstar = slot(j) + 6 * st;
+            if (p.has_mesh) {
+                q.cdata = slot(j) + 9 * st;
+                q.cbits = bits(j);
+            }
+            e = launch_substep(q, s);
+        }
+        AdjArgs a{};
+        a.lS = ro->lam + 6 * st;
+        a.lvp = ro->lam + 9 * st;
+        a.lx = ro->lam;
+        a.lv = ro->lam + 3 * st;
+        a.gks = ro->gslot;
+        a.gkd = ro->gslot + 6 * st;
+        for (int j = nsub; j >= 0 && e == cudaSuccess; j--) {
+            // spring part: substep j (j < nsub); contact part: substep j - 1 (j > 0)
+            if (j < nsub) {
+                a.xs_s = xstart(j);
+                a.lF_s = lF2[j & 1];
+            }
+            if (j > 0) {
+                a.xs_c = xstart(j - 1);
+                a.vs_c = slot(j - 1) + 6 * st;
+                a.cd_c = slot(j - 1) + 9 * st;
+                a.cb_c = p.has_mesh ? bits(j - 1) : nullptr;
+                a.lF_c = lF2[(j - 1) & 1];
+            }
+            if (j == nsub)
+                e = launch_pdl(adj_kernel<false, true>, blocks, s, p, a);
+            else if (j > 0)
+                e = launch_pdl(adj_kernel<true, true>, blocks, s, p, a);
+            else
+                e = launch_pdl(adj_kernel<true, false>, blocks, s, p, a);
+        }
+    }
+    return e;
+}
+
+// Captures body(stream) on the cloth's capture stream into *exec.
+template <typename F>
+cudaError_t capture_graph(ClothHandle *h, cudaGraphExec_t *exec, F &&body)
+{
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t le = body(h->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+// Runs the forward chain or the reverse pass on s, through a cached graph
+// unless the cloth was created with CLOTH_FLAG_NO_GRAPH.
+cudaError_t run_pass(ClothRollout *ro, bool backward, cudaStream_t s)
+{
+    ClothHandle *h = ro->h;
+    auto body = [ro, backward](cudaStream_t cs) {
+        return backward ? enqueue_backward(ro, cs) : enqueue_forward(ro, cs);
+    };
+    if (h->desc.flags & CLOTH_FLAG_NO_GRAPH) return body(s);
+    cudaGraphExec_t &gx = backward ? ro->bwd_graph : ro->fwd_graph;
+    unsigned long long &gen = backward ? ro->bwd_gen : ro->fwd_gen;
+    if (gx && gen != h->params_gen) {
+        cudaGraphExecDestroy(gx);
+        gx = nullptr;
+    }
+    if (!gx) {
+        const cudaError_t e = capture_graph(h, &gx, body);
+        if (e != cudaSuccess) {
+            gx = nullptr;
+            return e;
+        }
+        gen = h->params_gen;
+    }
+    return cudaGraphLaunch(gx, s);
+}
 
 }  // namespace
 
@@ -274,6 +527,9 @@ int cloth_rollout_create(ClothHandle *h, int32_t nsteps, int32_t checkpoint_ever
     std::vector<float> ks, kd;
     try {
         ro->kseg.resize((size_t)ro->nseg + 2);
+        for (int g = 0; g <= ro->nseg; g++)
+            ro->kseg[g] = ro->k0 + (unsigned long long)g * ro->every * d.substeps;
+        ro->k_final = ro->k0 + (unsigned long long)nsteps * d.substeps;
         // canonical order -> slot index, and per-type constants for missing slots
         const int type[CLOTH_NDIR] = {0, 0, 1, 1, 2, 2};
         for (long long r = 0; r < d.ny; r++)
@@ -290,12 +546,16 @@ int cloth_rollout_create(ClothHandle *h, int32_t nsteps, int32_t checkpoint_ever
         return rfail(CLOTH_ERR_OOM, "host allocation failed");
     }
     ro->S = (int)map.size();
-    const size_t seg_sub = (size_t)ro->every * d.substeps;
+    const size_t seg_sub = (size_t)ro->every * d.substeps + 1;
     if (e == cudaSuccess) e = cudaMalloc(&ro->x0, sizeof(float) * 3 * (size_t)N);
     if (e == cudaSuccess) e = cudaMalloc(&ro->v0, sizeof(float) * 3 * (size_t)N);
     if (e == cudaSuccess) e = cudaMalloc(&ro->ckpt, sizeof(float) * 6 * (size_t)st * (size_t)ro->nseg);
-    if (e == cudaSuccess) e = cudaMalloc(&ro->seg, sizeof(float) * 9 * (size_t)st * seg_sub);
-    if (e == cudaSuccess) e = cudaMalloc(&ro->lam, sizeof(float) * 15 * (size_t)st);
+    if (e == cudaSuccess) e = cudaMalloc(&ro->seg, sizeof(float) * SLOT_PLANES * (size_t)st * seg_sub);
+    // the padding columns of the recompute slots match the cloth's (zero) ones
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ro->seg, 0, sizeof(float) * SLOT_PLANES * (size_t)st * seg_sub, h->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&ro->cbits, sizeof(uint32_t) * (size_t)(st / 32) * seg_sub);
+    if (e == cudaSuccess) e = cudaMalloc(&ro->lam, sizeof(float) * 18 * (size_t)st);
     if (e == cudaSuccess) e = cudaMalloc(&ro->gslot, sizeof(double) * 12 * (size_t)st);
     if (e == cudaSuccess) e = cudaMalloc(&ro->final_state, sizeof(float) * 6 * (size_t)st);
     if (e == cudaSuccess) e = cudaMalloc(&ro->map, sizeof(int) * (size_t)(ro->S > 0 ? ro->S : 1));
@@ -359,20 +619,8 @@ int cloth_rollout_forward(ClothRollout *ro, const float *d_ks, const float *d_kd
     RTRY(h, launch_aos_to_soa(ro->x0, d_v0 ? d_v0 : ro->v0, h->state, h->state + 6 * st, st, h->n, h->desc.nx,
                               h->pitch, h->ctrl, s),
          "initial state");
-    unsigned long long k = ro->k0;
-    for (int g = 0; g < ro->nseg; g++) {
-        ro->kseg[g] = k;
-        RTRY(h, cudaMemcpyAsync(ro->ckpt + (size_t)g * 6 * st, cur_state(h, k), sizeof(float) * 6 * st,
-                                cudaMemcpyDeviceToDevice, s),
-             "checkpoint");
-        const int steps = (g == ro->nseg - 1) ? ro->nsteps - g * ro->every : ro->every;
-        for (int q = 0; q < steps * h->desc.substeps; q++) RTRY(h, launch_substep(h->params, s), "substep");
-        k += (unsigned long long)steps * h->desc.substeps;
-    }
-    ro->k_final = k;
-    h->substeps_done = (long long)k;
-    RTRY(h, cudaMemcpyAsync(ro->final_state, cur_state(h, k), sizeof(float) * 6 * st, cudaMemcpyDeviceToDevice, s),
-         "save final state");
+    RTRY(h, run_pass(ro, false, s), "forward chain");
+    h->substeps_done = (long long)ro->k_final;
     if (d_pos_out || d_vel_out)
         RTRY(h, launch_soa_to_aos(h->state, h->state + 6 * st, st, h->n, h->desc.nx, h->pitch, h->ctrl, d_pos_out,
                                   d_vel_out, s),
@@ -389,44 +637,15 @@ int cloth_rollout_backward(ClothRollout *ro, const float *d_gpos, const float *d
     if (h->dead) return rfail(CLOTH_ERR_STATE, "handle unusable after an earlier CUDA error");
     if (!ro->forward_done) return rfail(CLOTH_ERR_INVALID_ARG, "cloth_rollout_backward before forward");
     const long long st = h->stride;
-    const int n = h->n, nx = h->desc.nx, sub = h->desc.substeps;
+    const int n = h->n, nx = h->desc.nx;
     cudaStream_t s = h->stream;
-    float *lx = ro->lam, *lv = ro->lam + 3 * st, *lS = ro->lam + 6 * st, *lvp = ro->lam + 9 * st,
-          *lF = ro->lam + 12 * st;
-    const long long total = (long long)h->desc.ny * h->pitch;
-    RTRY(h, cudaMemsetAsync(ro->lam, 0, sizeof(float) * 15 * st, s), "clear adjoints");
+    float *lx = ro->lam, *lv = ro->lam + 3 * st;
+    RTRY(h, cudaMemsetAsync(ro->lam, 0, sizeof(float) * 18 * st, s), "clear adjoints");
     RTRY(h, cudaMemsetAsync(ro->gslot, 0, sizeof(double) * 12 * st, s), "clear gradients");
     aos_planes_kernel<<<nblk(n, 256), 256, 0, s>>>(d_gpos, n, nx, h->pitch, st, lx);
     aos_planes_kernel<<<nblk(n, 256), 256, 0, s>>>(d_gvel, n, nx, h->pitch, st, lv);
     RTRY(h, cudaGetLastError(), "load output adjoints");
-    StepParams p = h->params;
-    for (int g = ro->nseg - 1; g >= 0; g--) {
-        const int steps = (g == ro->nseg - 1) ? ro->nsteps - g * ro->every : ro->every;
-        const int nsub = steps * sub;
-        const unsigned long long kg = ro->kseg[g];
-        // restore the checkpoint and recompute the segment, keeping every
-        // substep's start state and post-integration velocity
-        RTRY(h, cudaMemcpyAsync(&h->ctrl->k, &ro->kseg[g], sizeof(unsigned long long), cudaMemcpyHostToDevice, s),
-             "set substep counter");
-        RTRY(h, cudaMemcpyAsync(cur_state(h, kg), ro->ckpt + (size_t)g * 6 * st, sizeof(float) * 6 * st,
-                                cudaMemcpyDeviceToDevice, s),
-             "restore checkpoint");
-        for (int j = 0; j < nsub; j++) {
-            float *sj = ro->seg + (size_t)j * 9 * st;
-            RTRY(h, cudaMemcpyAsync(sj, cur_state(h, kg + j), sizeof(float) * 6 * st, cudaMemcpyDeviceToDevice, s),
-                 "store substep state");
-            StepParams q = p;
-            q.vstar = sj + 6 * st;
-            RTRY(h, launch_substep(q, s), "recompute substep");
-        }
-        for (int j = nsub - 1; j >= 0; j--) {
-            const float *sj = ro->seg + (size_t)j * 9 * st;
-            adj_contact_kernel<<<nblk(total, 256), 256, 0, s>>>(p, sj, sj + 6 * st, lx, lv, lS, lvp, lF);
-            adj_spring_kernel<<<nblk(total, 256), 256, 0, s>>>(p, sj, lF, lS, lvp, lx, lv, ro->gslot,
-                                                               ro->gslot + 6 * st);
-            RTRY(h, cudaGetLastError(), "reverse substep");
-        }
-    }
+    RTRY(h, run_pass(ro, true, s), "reverse pass");
     if (d_gv0) planes_aos_kernel<<<nblk(n, 256), 256, 0, s>>>(lv, n, nx, h->pitch, st, d_gv0);
     if (d_gks) gather_kernel<<<nblk(ro->S, 256), 256, 0, s>>>(ro->gslot, ro->map, ro->S, d_gks);
     if (d_gkd) gather_kernel<<<nblk(ro->S, 256), 256, 0, s>>>(ro->gslot + 6 * st, ro->map, ro->S, d_gkd);
@@ -434,9 +653,7 @@ int cloth_rollout_backward(ClothRollout *ro, const float *d_gpos, const float *d
     // leave the cloth in its final forward state
     RTRY(h, cudaMemcpyAsync(&h->ctrl->k, &ro->k_final, sizeof(unsigned long long), cudaMemcpyHostToDevice, s),
          "set substep counter");
-    RTRY(h, cudaMemcpyAsync(cur_state(h, ro->k_final), ro->final_state, sizeof(float) * 6 * st,
-                            cudaMemcpyDeviceToDevice, s),
-         "restore final state");
+    RTRY(h, copy_planes(ro->final_state, cur_state(h, ro->k_final), 6 * st, s), "restore final state");
     return CLOTH_OK;
 }
 
@@ -444,10 +661,13 @@ void cloth_rollout_destroy(ClothRollout *ro)
 {
     if (!ro) return;
     if (ro->h) cudaStreamSynchronize(ro->h->stream);
+    if (ro->fwd_graph) cudaGraphExecDestroy(ro->fwd_graph);
+    if (ro->bwd_graph) cudaGraphExecDestroy(ro->bwd_graph);
     cudaFree(ro->x0);
     cudaFree(ro->v0);
     cudaFree(ro->ckpt);
     cudaFree(ro->seg);
+    cudaFree(ro->cbits);
     cudaFree(ro->lam);
     cudaFree(ro->gslot);
     cudaFree(ro->final_state);

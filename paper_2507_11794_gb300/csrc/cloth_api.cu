@@ -100,6 +100,7 @@ void cloth_fill_params(ClothHandle *h)
 {
     const ClothDesc &d = h->desc;
     StepParams &p = h->params;
+    h->params_gen++;
     p.nx = d.nx;
     p.ny = d.ny;
     p.n = h->n;

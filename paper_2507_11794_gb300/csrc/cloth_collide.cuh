@@ -161,11 +161,38 @@ struct CollShared {
     int base[COLL_WARPS][32];    // first candidate index of each lane (warp exclusive scan)
     float val[COLL_WARPS][32];   // one round's results: max(t - delta, 0) on a hit, else -1
 };
+// The recording variant adds each candidate's terms of g1 and g2.
+struct CollSharedRec : CollShared {
+    float g[COLL_WARPS][6][32];
+};
+
+// Records the response data of a hit node at plane offset o for the reverse
+// pass: m, r, g1 / K, g2 / K (the factors it multiplies by the adjoints) and
+// the node's bit.
+__device__ __forceinline__ void coll_record(const StepParams &p, long long o, float m, float K, float rx, float ry,
+                                            float rz, const float g1[3], const float g2[3])
+{
+    const long long st = p.stride;
+    const float invK = 1.0f / K;
+    float *cd = p.cdata;
+    cd[o] = m;
+    cd[st + o] = rx;
+    cd[2 * st + o] = ry;
+    cd[3 * st + o] = rz;
+    cd[4 * st + o] = g1[0] * invK;
+    cd[5 * st + o] = g1[1] * invK;
+    cd[6 * st + o] = g1[2] * invK;
+    cd[7 * st + o] = g2[0] * invK;
+    cd[8 * st + o] = g2[1] * invK;
+    cd[9 * st + o] = g2[2] * invK;
+    atomicOr(p.cbits + (o >> 5), 1u << (o & 31));
+}
 
 // Src supplies per list entry i: entry(i, cloth, offset) and params(cloth).
-template <class Src>
-__device__ __forceinline__ void collide_list(const Src &src, CollShared &sh, unsigned long long k, unsigned n,
-                                             float &fsum)
+// REC (with CollSharedRec): also sums, over the active hits in the same
+// order, g1 and g2 as collide_t<true> does and records them (coll_record).
+template <bool REC = false, class Src, class Sh>
+__device__ __forceinline__ void collide_list(const Src &src, Sh &sh, unsigned long long k, unsigned n, float &fsum)
 {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned long long nw = (unsigned long long)gridDim.x * COLL_WARPS;
@@ -221,9 +248,11 @@ __device__ __forceinline__ void collide_list(const Src &src, CollShared &sh, uns
         __syncwarp();
         float acc = 0.0f;
         int K = 0;
+        float g1[3] = {0.0f, 0.0f, 0.0f}, g2[3] = {0.0f, 0.0f, 0.0f};
         for (int r0 = 0; r0 < total; r0 += 32) {
             const int j = r0 + lane;
             float val = -1.0f;
+            float gn[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
             if (j < total) {
                 // owner: the last lane whose first candidate is <= j (it has cnt > 0)
                 int ow = 0;
@@ -241,10 +270,24 @@ __device__ __forceinline__ void collide_list(const Src &src, CollShared &sh, uns
                 const StepParams &lp = src.params(__float_as_int(L.r.w));
                 float th, f;
                 float4 A, B, C;
-                if (coll_candidate(lp, lq, e, cx, cy, cz, L.box.x, L.box.y, L.box.z, th, f, A, B, C))
+                if (coll_candidate(lp, lq, e, cx, cy, cz, L.box.x, L.box.y, L.box.z, th, f, A, B, C)) {
                     val = fmaxf(th - lp.delta, 0.0f);
+                    if (REC) {
+                        // the terms collide_t<true> adds for an active hit (t - delta > 0)
+                        const float nx = B.y * C.z - B.z * C.y, ny = B.z * C.x - B.x * C.z,
+                                    nz = B.x * C.y - B.y * C.x;
+                        gn[0] = nx * f; gn[1] = ny * f; gn[2] = nz * f;
+                        gn[3] = th * nx * f; gn[4] = th * ny * f; gn[5] = th * nz * f;
+                    }
+                }
             }
             sh.val[wib][lane] = val;
+            if constexpr (REC) {
+                if (val > 0.0f) {
+#pragma unroll
+                    for (int t = 0; t < 6; t++) sh.g[wib][t][lane] = gn[t];
+                }
+            }
             __syncwarp();
             if (cnt > 0) {
                 const int q0 = max(excl, r0), q1 = min(excl + cnt, r0 + 32);
@@ -253,6 +296,14 @@ __device__ __forceinline__ void collide_list(const Src &src, CollShared &sh, uns
                     if (v >= 0.0f) {
                         acc += v;
                         K++;
+                        if constexpr (REC) {
+                            if (v > 0.0f) {
+                                g1[0] += sh.g[wib][0][t - r0]; g1[1] += sh.g[wib][1][t - r0];
+                                g1[2] += sh.g[wib][2][t - r0];
+                                g2[0] += sh.g[wib][3][t - r0]; g2[1] += sh.g[wib][4][t - r0];
+                                g2[2] += sh.g[wib][5][t - r0];
+                            }
+                        }
                     }
                 }
             }
@@ -263,7 +314,13 @@ __device__ __forceinline__ void collide_list(const Src &src, CollShared &sh, uns
         float ox, oy, oz;
         bool hit;
         if (serial) {
-            hit = collide_t<false>(p, sx, sy, sz, ex, ey, ez, ox, oy, oz);
+            if (REC) {
+                float sg1[3] = {0.0f, 0.0f, 0.0f}, sg2[3] = {0.0f, 0.0f, 0.0f}, mK[5];
+                hit = collide_t<true>(p, sx, sy, sz, ex, ey, ez, ox, oy, oz, sg1, sg2, mK);
+                if (hit) coll_record(p, o, mK[0], mK[1], mK[2], mK[3], mK[4], sg1, sg2);
+            } else {
+                hit = collide_t<false>(p, sx, sy, sz, ex, ey, ez, ox, oy, oz);
+            }
         } else {
             hit = K > 0;
             if (hit) {
@@ -271,6 +328,7 @@ __device__ __forceinline__ void collide_list(const Src &src, CollShared &sh, uns
                 ox = sx + m * q.rx;
                 oy = sy + m * q.ry;
                 oz = sz + m * q.rz;
+                if (REC) coll_record(p, o, m, (float)K, q.rx, q.ry, q.rz, g1, g2);
             }
         }
         if (hit) {

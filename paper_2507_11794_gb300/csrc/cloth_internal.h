@@ -58,6 +58,8 @@ struct StepParams {
     int *coll_list;            // node offsets marked for the collision kernel (capacity N)
     int *coll_cloth;           // batch mode: cloth index of each entry (nullptr for one cloth)
     float *vstar;              // optional 3 planes: velocity after integration (adjoint recompute)
+    float *cdata;              // optional 10 planes: per hit node m, r, g1 / K, g2 / K (adjoint recompute)
+    uint32_t *cbits;           // with cdata: one bit per plane offset, set for the nodes that hit
     float4 *force;             // per-node force buffer of the atomic spring path, or nullptr
     float4 *edge_resp;         // edge narrow phase: per list entry (response position, hit flag), or nullptr
     unsigned *coll_count;      // entries in coll_list (reset by the collision kernel)
@@ -184,6 +186,7 @@ struct ClothHandle {
     bool has_mesh = false;
     StepParams params{};
     cudaGraphExec_t graph = nullptr;
+    unsigned long long params_gen = 0;  // bumped by cloth_fill_params: graphs built from older params are stale
     long long substeps_done = 0;
     bool dead = false;
 };

@@ -517,9 +517,12 @@ struct OneClothList {
 
 // Collision pass over the nodes the walk listed (cooperative, see
 // collide_list); the last CTA resets the list and advances the substep counter.
+// REC: the adjoint recompute's variant, which also records each hit's
+// response data (p.cdata, p.cbits).
+template <bool REC>
 __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kernel(const __grid_constant__ StepParams p)
 {
-    __shared__ CollShared sh;
+    __shared__ std::conditional_t<REC, CollSharedRec, CollShared> sh;
     __shared__ unsigned long long s_k;
     __shared__ unsigned s_n;
     pdl_launch_dependents();
@@ -531,7 +534,7 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kern
     __syncthreads();
     const unsigned long long k = s_k;
     float fsum = 0.0f;
-    collide_list(OneClothList{p}, sh, k, s_n, fsum);
+    collide_list<REC>(OneClothList{p}, sh, k, s_n, fsum);
     if (__any_sync(FULL, !isfinite(fsum)) && (threadIdx.x & 31) == 0)
         atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
     __syncthreads();
@@ -804,7 +807,8 @@ cudaError_t launch_collide(const StepParams &p, cudaStream_t s)
         if (e != cudaSuccess) return e;
         return launch_k(edge_apply_kernel, p.coll_blocks, 256, s, p);
     }
-    return launch_k(collide_kernel, p.coll_blocks, 32 * COLL_WARPS, s, p);
+    if (p.cdata) return launch_k(collide_kernel<true>, p.coll_blocks, 32 * COLL_WARPS, s, p);
+    return launch_k(collide_kernel<false>, p.coll_blocks, 32 * COLL_WARPS, s, p);
 }
 
 cudaError_t launch_substep(const StepParams &p, cudaStream_t s)

@@ -5,6 +5,8 @@ differences at the full differentiation workload.
 Elementwise metric: rel err = |g - g_ref| / max(|g_ref|, 1e-3 max_k |g_ref,k|);
 each test states its bound and why.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -223,3 +225,57 @@ def test_config4_gradients(cloth_lib, oracle_lib):
     assert len(got) == 32
     rel = np.abs(np.array(got) - np.array(fds)) / np.maximum(np.abs(fds), floor)
     assert np.max(rel) <= 1e-3, rel
+
+
+def _grads_twice(P, sc, tgt, nsteps, every, flags=0, swap_mesh=None):
+    """Two forward/backward passes of one rollout (the second replays any
+    cached graphs); optionally replaces the cloth's mesh between them."""
+    from paper_2507_11794_gb300.rollout import Rollout
+    outs = []
+    with P.Cloth(sc, flags=flags) as cl:
+        ro = Rollout(cl, nsteps, every)
+        for it in range(2):
+            if it == 1 and swap_mesh is not None:
+                cl.set_mesh(*swap_mesh)
+            k = torch.tensor(sc.ks_spring, dtype=torch.float32, device="cuda", requires_grad=True)
+            d = torch.tensor(sc.kd_spring, dtype=torch.float32, device="cuda", requires_grad=True)
+            v = torch.tensor(sc.init_vel.astype(np.float32), device="cuda", requires_grad=True)
+            pos, vel = ro(k, d, v)
+            loss = ((pos - torch.tensor(tgt, dtype=torch.float32, device="cuda")) ** 2).sum(1).mean()
+            loss.backward()
+            outs.append((k.grad.cpu().numpy(), d.grad.cpu().numpy(), v.grad.cpu().numpy(),
+                         pos.detach().cpu().numpy()))
+        ro.close()
+    return outs
+
+
+def test_rollout_graphs_match_direct_launches(cloth_lib):
+    # The forward chain and the reverse pass replayed from CUDA graphs give
+    # the same bits as the same launches issued one by one
+    # (CLOTH_FLAG_NO_GRAPH), on the first call and on replays; a segment
+    # shorter than the others (10 steps, checkpoints every 4) is covered.
+    P = cloth_lib
+    rng = np.random.default_rng(13)
+    sc, _ = _scene("contact", rng)
+    tgt = sc.init_pos + rng.normal(0, 0.01, sc.init_pos.shape)
+    a = _grads_twice(P, sc, tgt, 10, 4)
+    b = _grads_twice(P, sc, tgt, 10, 4, flags=P.capi.CLOTH_FLAG_NO_GRAPH)
+    for x in (a[0], a[1], b[1]):
+        for u, w in zip(x, b[0]):
+            assert np.array_equal(u, w)
+
+
+def test_rollout_follows_a_mesh_change(cloth_lib):
+    # Replacing the mesh after the rollout captured its graphs rebuilds them:
+    # the second pass matches a fresh rollout over the new mesh (here: no
+    # mesh, so the falling cloth meets nothing).
+    P = cloth_lib
+    rng = np.random.default_rng(14)
+    sc, _ = _scene("contact", rng)
+    tgt = sc.init_pos + rng.normal(0, 0.01, sc.init_pos.shape)
+    a = _grads_twice(P, sc, tgt, 10, 4, swap_mesh=(None, None))
+    free = dataclasses.replace(sc, mesh_verts=None, mesh_tris=None)
+    b = _grads_twice(P, free, tgt, 10, 4)
+    assert not np.array_equal(a[0][3], a[1][3])  # the contact changed the result
+    for u, w in zip(a[1], b[0]):
+        assert np.array_equal(u, w)
