@@ -15,6 +15,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <initializer_list>
 #include <new>
 #include <vector>
 
@@ -115,14 +116,17 @@ __device__ __forceinline__ void spring_adj(const float *xo, const float *vo, con
     gkd = um * ud;
 }
 
-// Reverse of the spring forces of one substep at node (r, c), offset o:
-// xs the substep's start state, lF its force adjoints (all nodes), lS / lvp
-// the node's own adjoint parts; returns the adjoints of the node's start
-// position (gx) and velocity (gv) and adds the gradients of the springs the
-// node owns.
-__device__ __forceinline__ void spring_adj_node(const StepParams &p, const float *__restrict__ xs,
-                                                const float *__restrict__ lF, const float *__restrict__ lS,
-                                                const float *__restrict__ lvp, long long o, int r, int c,
+// Reverse of the spring forces of one substep at node (r, c), offset o, as
+// lane q (0..3) of the node's group of four lanes: the lane takes springs
+// u = q, q + 4, q + 8 of the node's twelve in the order (owned d, incoming d,
+// owned d + 1, ...), so lanes 0 and 2 take owned springs and write their
+// ks / kd gradients, lanes 1 and 3 incoming ones.  xs is the substep's start
+// state, lF its force adjoints (all nodes).  Returns the lane's part of the
+// adjoints of the node's start position (gx) and velocity (gv).  Loads are
+// issued unconditionally (a missing neighbour reads the node itself) so that
+// the lane's gathers overlap; a missing spring's terms are discarded.
+__device__ __forceinline__ void spring_adj_lane(const StepParams &p, const float *__restrict__ xs,
+                                                const float *__restrict__ lF, long long o, int r, int c, int q,
                                                 double *__restrict__ gks, double *__restrict__ gkd, float gx[3],
                                                 float gv[3])
 {
@@ -130,48 +134,42 @@ __device__ __forceinline__ void spring_adj_node(const StepParams &p, const float
     const float xi[3] = {xs[o], xs[st + o], xs[2 * st + o]};
     const float vi[3] = {xs[3 * st + o], xs[4 * st + o], xs[5 * st + o]};
     const float fi[3] = {lF[o], lF[st + o], lF[2 * st + o]};
-    gx[0] = lS[o]; gx[1] = lS[st + o]; gx[2] = lS[2 * st + o];
-    gv[0] = lvp[o]; gv[1] = lvp[st + o]; gv[2] = lvp[2 * st + o];
-    // Gather first, compute after: every load is issued unconditionally (a
-    // missing neighbour reads the node itself) so that the twelve springs'
-    // loads are all in flight together; a missing spring's terms are
-    // discarded by the validity selects.  Spring t < 6: owned, direction t;
-    // t >= 6: incoming along direction t - 6.
-    float xn[12][3], vn[12][3], ln[12][3], ksn[12], kdn[12];
-    double sk[CLOTH_NDIR], sd[CLOTH_NDIR];
-    bool ok[12];
+    const bool own = (q & 1) == 0;
+    float xn[3][3], vn[3][3], ln[3][3], ksn[3], kdn[3];
+    double sk[3], sd[3];
+    bool ok[3];
+    int dd[3];
 #pragma unroll
-    for (int t = 0; t < 12; t++) {
-        const int d = t < 6 ? t : t - 6;
-        const int r2 = t < 6 ? r + dev_dr(d) : r - dev_dr(d);
-        const int c2 = t < 6 ? c + dev_dc(d) : c - dev_dc(d);
+    for (int t = 0; t < 3; t++) {
+        const int d = (q >> 1) + 2 * t;
+        dd[t] = d;
+        const int r2 = own ? r + dev_dr(d) : r - dev_dr(d);
+        const int c2 = own ? c + dev_dc(d) : c - dev_dc(d);
         ok[t] = r2 >= 0 && r2 < p.ny && c2 >= 0 && c2 < p.nx;
         const long long e = ok[t] ? (long long)r2 * p.pitch + c2 : o;
         xn[t][0] = xs[e]; xn[t][1] = xs[st + e]; xn[t][2] = xs[2 * st + e];
         vn[t][0] = xs[3 * st + e]; vn[t][1] = xs[4 * st + e]; vn[t][2] = xs[5 * st + e];
         ln[t][0] = lF[e]; ln[t][1] = lF[st + e]; ln[t][2] = lF[2 * st + e];
-        const long long so = d * st + (t < 6 ? o : e);  // the spring's slot: its owner's offset
+        const long long so = d * st + (own ? o : e);  // the spring's slot: its owner's offset
         ksn[t] = p.ks_slot[so];
         kdn[t] = p.kd_slot[so];
-        if (t < 6) {
-            sk[d] = gks[so];
-            sd[d] = gkd[so];
-        }
+        sk[t] = own ? gks[so] : 0.0;
+        sd[t] = own ? gkd[so] : 0.0;
     }
+    gx[0] = gx[1] = gx[2] = gv[0] = gv[1] = gv[2] = 0.0f;
 #pragma unroll
-    for (int u = 0; u < 12; u++) {
-        // the order of the sums: owned d, incoming d, owned d + 1, ...
-        const int d = u >> 1, t = (u & 1) ? d + 6 : d;
+    for (int t = 0; t < 3; t++) {
+        const int d = dd[t];
         float a[3], b[3], g1, g2;
-        if (t < 6) {
+        if (own) {
             const float mu[3] = {fi[0] - ln[t][0], fi[1] - ln[t][1], fi[2] - ln[t][2]};
             spring_adj(xi, vi, xn[t], vn[t], mu, ksn[t], kdn[t], p.L0[d], a, b, g1, g2);
             if (ok[t]) {
                 gx[0] -= a[0]; gx[1] -= a[1]; gx[2] -= a[2];
                 gv[0] -= b[0]; gv[1] -= b[1]; gv[2] -= b[2];
                 // per-spring sums over the substeps in double: FP64 only in these reductions
-                gks[d * st + o] = sk[d] + (double)g1;
-                gkd[d * st + o] = sd[d] + (double)g2;
+                gks[d * st + o] = sk[t] + (double)g1;
+                gkd[d * st + o] = sd[t] + (double)g2;
             }
         } else {
             const float mu[3] = {ln[t][0] - fi[0], ln[t][1] - fi[1], ln[t][2] - fi[2]};
@@ -198,26 +196,45 @@ struct AdjArgs {
     double *gks, *gkd;      // per-spring gradient sums
 };
 
-// One reverse launch, one thread per node.  SPRING: the spring reverse of
-// substep j gives the node's start-state adjoints; CONTACT: the response and
-// Euler reverse of the substep before (of the substep given, without
-// SPRING) consumes them at once.  Reversing a segment of n substeps takes
-// n + 1 launches: contact(n-1), then spring(j) + contact(j-1) for
+// One reverse launch, four lanes per node.  SPRING: the spring reverse of
+// substep j (the lanes' parts summed as lS + ((q0 + q1) + (q2 + q3))) gives
+// the node's start-state adjoints; CONTACT: lane 0 then runs the response
+// and Euler reverse of the substep before (of the substep given, without
+// SPRING), which consumes them at once.  Reversing a segment of n substeps
+// takes n + 1 launches: contact(n-1), then spring(j) + contact(j-1) for
 // j = n-1..1, then spring(0).
 constexpr int ADJ_THREADS = 128;
+constexpr int ADJ_LANES = 4;  // lanes per node
 template <bool SPRING, bool CONTACT>
 __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(const StepParams p, const AdjArgs a)
 {
     pdl_enter();
     const long long st = p.stride;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long idx = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / ADJ_LANES;
+    const int q = threadIdx.x % ADJ_LANES;
+    // the group's four lanes share idx, so they leave or stay together
     if (idx >= (long long)p.ny * p.pitch) return;
     const int r = (int)(idx / p.pitch), c = (int)(idx % p.pitch);
     if (c >= p.nx) return;
+    if (!SPRING && q != 0) return;
     const long long o = idx;
     float l[3], m[3];
     if (SPRING) {
-        spring_adj_node(p, a.xs_s, a.lF_s, a.lS, a.lvp, o, r, c, a.gks, a.gkd, l, m);
+        const unsigned gm = 0xFu << (threadIdx.x & 28u);  // the group's lanes
+        spring_adj_lane(p, a.xs_s, a.lF_s, o, r, c, q, a.gks, a.gkd, l, m);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            l[k] += __shfl_xor_sync(gm, l[k], 1);
+            m[k] += __shfl_xor_sync(gm, m[k], 1);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            l[k] += __shfl_xor_sync(gm, l[k], 2);
+            m[k] += __shfl_xor_sync(gm, m[k], 2);
+        }
+        if (q != 0) return;
+        l[0] = a.lS[o] + l[0]; l[1] = a.lS[st + o] + l[1]; l[2] = a.lS[2 * st + o] + l[2];
+        m[0] = a.lvp[o] + m[0]; m[1] = a.lvp[st + o] + m[1]; m[2] = a.lvp[2 * st + o] + m[2];
     } else {
         l[0] = a.lx[o]; l[1] = a.lx[st + o]; l[2] = a.lx[2 * st + o];
         m[0] = a.lv[o]; m[1] = a.lv[st + o]; m[2] = a.lv[2 * st + o];
@@ -294,8 +311,11 @@ struct ClothRollout {
     std::vector<unsigned long long> kseg;  // substep counter at each checkpoint (host copies for async uploads)
     float *x0 = nullptr, *v0 = nullptr;    // initial state, AoS [N][3]
     float *ckpt = nullptr;                 // nseg x 6 planes
-    float *seg = nullptr;                  // every*substeps+1 slots x 19 planes (x, v, v*, response data)
+    float *seg = nullptr;                  // 2 sets x (every*substeps+1) slots x 19 planes (x, v, v*, response data)
     uint32_t *cbits = nullptr;             // every*substeps+1 slots x stride/32 hit-bit words
+    size_t seg_slots = 0;                  // slots per recompute set (two sets: seg and cbits hold both)
+    cudaStream_t side = nullptr;           // the reverse chain of the backward pass
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
     float *lam = nullptr;                  // lx, lv, lS, lvp, lF (two buffers): 18 planes
     double *gslot = nullptr;               // gks, gkd: 12 planes (double sums over substeps)
     float *final_state = nullptr;          // 6 planes
@@ -374,81 +394,124 @@ cudaError_t enqueue_forward(ClothRollout *ro, cudaStream_t s)
     return e;
 }
 
-// The reverse pass over all segments, last first.  Each segment is
-// recomputed from its checkpoint with the substep kernels redirected:
-// substep j reads slot j (the checkpoint for j = 0) and writes slot j + 1 and
-// its post-integration velocity into slot j, so every substep's start state
-// stays in place without copies; the state buffers of the cloth are not
-// touched.  The reverse launches then walk the slots backwards, the force
-// adjoints of consecutive substeps alternating between two buffers.
-cudaError_t enqueue_backward(ClothRollout *ro, cudaStream_t s)
+// Slot j of recompute set b (segments alternate between the two sets).
+float *seg_slot(const ClothRollout *ro, int b, int j)
+{
+    return ro->seg + ((size_t)b * ro->seg_slots + (size_t)j) * SLOT_PLANES * ro->h->stride;
+}
+uint32_t *seg_bits(const ClothRollout *ro, int b, int j)
+{
+    return ro->cbits + ((size_t)b * ro->seg_slots + (size_t)j) * (size_t)(ro->h->stride / 32);
+}
+
+// Recompute of segment g from its checkpoint into slot set g & 1, with the
+// substep kernels redirected: substep j reads slot j (the checkpoint for
+// j = 0) and writes slot j + 1, its post-integration velocity and, for the
+// nodes that hit, the response data into slot j; every substep's start state
+// stays in place without copies and the cloth's state buffers are not
+// touched.
+cudaError_t recompute_segment(ClothRollout *ro, int g, cudaStream_t s)
 {
     ClothHandle *h = ro->h;
     const long long st = h->stride;
-    const int sub = h->desc.substeps;
-    float *lF2[2] = {ro->lam + 12 * st, ro->lam + 15 * st};
-    const int blocks = nblk((long long)h->desc.ny * h->pitch, ADJ_THREADS);
+    const int b = g & 1, nsub = seg_steps(ro, g) * h->desc.substeps;
+    const unsigned long long kg = ro->kseg[g];
+    const float *ck = ro->ckpt + (size_t)g * 6 * st;
     const StepParams &p = h->params;
-    cudaError_t e = cudaSuccess;
-    for (int g = ro->nseg - 1; g >= 0 && e == cudaSuccess; g--) {
-        const int nsub = seg_steps(ro, g) * sub;
-        const unsigned long long kg = ro->kseg[g];
-        const float *ck = ro->ckpt + (size_t)g * 6 * st;
-        auto slot = [&](int j) { return ro->seg + (size_t)j * SLOT_PLANES * st; };
-        auto xstart = [&](int j) { return j == 0 ? ck : (const float *)slot(j); };
-        auto bits = [&](int j) { return ro->cbits + (size_t)j * (st / 32); };
-        const long long nwords = (long long)nsub * (st / 32);
-        const int zb = nblk(nwords, 256);
-        segment_begin_kernel<<<zb < 1 ? 1 : (zb > 1024 ? 1024 : zb), 256, 0, s>>>(h->ctrl, kg, ro->cbits, nwords);
-        e = cudaGetLastError();
-        for (int j = 0; j < nsub && e == cudaSuccess; j++) {
-            StepParams q = p;
-            float *in = const_cast<float *>(xstart(j));
-            float *out = slot(j + 1);
-            // the kernels read (k odd ? state1 : state0) and write the other
-            if ((kg + (unsigned long long)j) & 1ull) {
-                q.state1 = in;
-                q.state0 = out;
-            } else {
-                q.state0 = in;
-                q.state1 = out;
-            }
-            q.vstar = slot(j) + 6 * st;
-            if (p.has_mesh) {
-                q.cdata = slot(j) + 9 * st;
-                q.cbits = bits(j);
-            }
-            e = launch_substep(q, s);
+    const long long nwords = (long long)nsub * (st / 32);
+    const int zb = nblk(nwords, 256);
+    segment_begin_kernel<<<zb < 1 ? 1 : (zb > 1024 ? 1024 : zb), 256, 0, s>>>(h->ctrl, kg, seg_bits(ro, b, 0),
+                                                                               nwords);
+    cudaError_t e = cudaGetLastError();
+    for (int j = 0; j < nsub && e == cudaSuccess; j++) {
+        StepParams q = p;
+        float *in = j == 0 ? const_cast<float *>(ck) : seg_slot(ro, b, j);
+        float *out = seg_slot(ro, b, j + 1);
+        // the kernels read (k odd ? state1 : state0) and write the other
+        if ((kg + (unsigned long long)j) & 1ull) {
+            q.state1 = in;
+            q.state0 = out;
+        } else {
+            q.state0 = in;
+            q.state1 = out;
         }
-        AdjArgs a{};
-        a.lS = ro->lam + 6 * st;
-        a.lvp = ro->lam + 9 * st;
-        a.lx = ro->lam;
-        a.lv = ro->lam + 3 * st;
-        a.gks = ro->gslot;
-        a.gkd = ro->gslot + 6 * st;
-        for (int j = nsub; j >= 0 && e == cudaSuccess; j--) {
-            // spring part: substep j (j < nsub); contact part: substep j - 1 (j > 0)
-            if (j < nsub) {
-                a.xs_s = xstart(j);
-                a.lF_s = lF2[j & 1];
-            }
-            if (j > 0) {
-                a.xs_c = xstart(j - 1);
-                a.vs_c = slot(j - 1) + 6 * st;
-                a.cd_c = slot(j - 1) + 9 * st;
-                a.cb_c = p.has_mesh ? bits(j - 1) : nullptr;
-                a.lF_c = lF2[(j - 1) & 1];
-            }
-            if (j == nsub)
-                e = launch_pdl(adj_kernel<false, true>, blocks, s, p, a);
-            else if (j > 0)
-                e = launch_pdl(adj_kernel<true, true>, blocks, s, p, a);
-            else
-                e = launch_pdl(adj_kernel<true, false>, blocks, s, p, a);
+        q.vstar = seg_slot(ro, b, j) + 6 * st;
+        if (p.has_mesh) {
+            q.cdata = seg_slot(ro, b, j) + 9 * st;
+            q.cbits = seg_bits(ro, b, j);
         }
+        e = launch_substep(q, s);
     }
     return e;
+}
+
+// Reverse of segment g over slot set g & 1, the force adjoints of
+// consecutive substeps alternating between two buffers.
+cudaError_t reverse_segment(ClothRollout *ro, int g, cudaStream_t s)
+{
+    ClothHandle *h = ro->h;
+    const long long st = h->stride;
+    const int b = g & 1, nsub = seg_steps(ro, g) * h->desc.substeps;
+    const float *ck = ro->ckpt + (size_t)g * 6 * st;
+    float *lF2[2] = {ro->lam + 12 * st, ro->lam + 15 * st};
+    const int blocks = nblk((long long)h->desc.ny * h->pitch * ADJ_LANES, ADJ_THREADS);
+    const StepParams &p = h->params;
+    auto xstart = [&](int j) { return j == 0 ? ck : (const float *)seg_slot(ro, b, j); };
+    AdjArgs a{};
+    a.lS = ro->lam + 6 * st;
+    a.lvp = ro->lam + 9 * st;
+    a.lx = ro->lam;
+    a.lv = ro->lam + 3 * st;
+    a.gks = ro->gslot;
+    a.gkd = ro->gslot + 6 * st;
+    cudaError_t e = cudaSuccess;
+    for (int j = nsub; j >= 0 && e == cudaSuccess; j--) {
+        // spring part: substep j (j < nsub); contact part: substep j - 1 (j > 0)
+        if (j < nsub) {
+            a.xs_s = xstart(j);
+            a.lF_s = lF2[j & 1];
+        }
+        if (j > 0) {
+            a.xs_c = xstart(j - 1);
+            a.vs_c = seg_slot(ro, b, j - 1) + 6 * st;
+            a.cd_c = seg_slot(ro, b, j - 1) + 9 * st;
+            a.cb_c = p.has_mesh ? seg_bits(ro, b, j - 1) : nullptr;
+            a.lF_c = lF2[(j - 1) & 1];
+        }
+        if (j == nsub)
+            e = launch_pdl(adj_kernel<false, true>, blocks, s, p, a);
+        else if (j > 0)
+            e = launch_pdl(adj_kernel<true, true>, blocks, s, p, a);
+        else
+            e = launch_pdl(adj_kernel<true, false>, blocks, s, p, a);
+    }
+    return e;
+}
+
+// The reverse pass over all segments, last first, as two chains: the
+// recomputes on s and the reverse launches on the rollout's side stream.
+// The reverse of segment g waits for its recompute; the recompute of
+// segment g - 1 runs meanwhile (into the other slot set) and the one of
+// g - 2 waits until the reverse of g has released its set.  Both chains are
+// latency-bound and occupy few SMs, so they overlap.
+cudaError_t enqueue_backward(ClothRollout *ro, cudaStream_t s)
+{
+    cudaStream_t v = ro->side;
+    cudaError_t e = cudaEventRecord(ro->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(v, ro->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    for (int g = ro->nseg - 1; g >= 0 && e == cudaSuccess; g--) {
+        if (g + 2 < ro->nseg) e = cudaStreamWaitEvent(s, ro->ev_rev[g & 1], 0);
+        if (e == cudaSuccess) e = recompute_segment(ro, g, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ro->ev_rec[g & 1], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(v, ro->ev_rec[g & 1], 0);
+        if (e == cudaSuccess) e = reverse_segment(ro, g, v);
+        if (e == cudaSuccess) e = cudaEventRecord(ro->ev_rev[g & 1], v);
+    }
+    // join the side stream back (also after an error, so that a capture ends)
+    const cudaError_t j1 = cudaEventRecord(ro->ev_join, v);
+    const cudaError_t j2 = j1 == cudaSuccess ? cudaStreamWaitEvent(s, ro->ev_join, 0) : j1;
+    return e != cudaSuccess ? e : j2;
 }
 
 // Captures body(stream) on the cloth's capture stream into *exec.
@@ -547,14 +610,18 @@ int cloth_rollout_create(ClothHandle *h, int32_t nsteps, int32_t checkpoint_ever
     }
     ro->S = (int)map.size();
     const size_t seg_sub = (size_t)ro->every * d.substeps + 1;
+    ro->seg_slots = seg_sub;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ro->side, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&ro->ev_fork, &ro->ev_join, &ro->ev_rec[0], &ro->ev_rec[1], &ro->ev_rev[0], &ro->ev_rev[1]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&ro->x0, sizeof(float) * 3 * (size_t)N);
     if (e == cudaSuccess) e = cudaMalloc(&ro->v0, sizeof(float) * 3 * (size_t)N);
     if (e == cudaSuccess) e = cudaMalloc(&ro->ckpt, sizeof(float) * 6 * (size_t)st * (size_t)ro->nseg);
-    if (e == cudaSuccess) e = cudaMalloc(&ro->seg, sizeof(float) * SLOT_PLANES * (size_t)st * seg_sub);
+    if (e == cudaSuccess) e = cudaMalloc(&ro->seg, sizeof(float) * SLOT_PLANES * (size_t)st * 2 * seg_sub);
     // the padding columns of the recompute slots match the cloth's (zero) ones
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(ro->seg, 0, sizeof(float) * SLOT_PLANES * (size_t)st * seg_sub, h->stream);
-    if (e == cudaSuccess) e = cudaMalloc(&ro->cbits, sizeof(uint32_t) * (size_t)(st / 32) * seg_sub);
+        e = cudaMemsetAsync(ro->seg, 0, sizeof(float) * SLOT_PLANES * (size_t)st * 2 * seg_sub, h->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&ro->cbits, sizeof(uint32_t) * (size_t)(st / 32) * 2 * seg_sub);
     if (e == cudaSuccess) e = cudaMalloc(&ro->lam, sizeof(float) * 18 * (size_t)st);
     if (e == cudaSuccess) e = cudaMalloc(&ro->gslot, sizeof(double) * 12 * (size_t)st);
     if (e == cudaSuccess) e = cudaMalloc(&ro->final_state, sizeof(float) * 6 * (size_t)st);
@@ -661,6 +728,7 @@ void cloth_rollout_destroy(ClothRollout *ro)
 {
     if (!ro) return;
     if (ro->h) cudaStreamSynchronize(ro->h->stream);
+    if (ro->side) cudaStreamSynchronize(ro->side);
     if (ro->fwd_graph) cudaGraphExecDestroy(ro->fwd_graph);
     if (ro->bwd_graph) cudaGraphExecDestroy(ro->bwd_graph);
     cudaFree(ro->x0);
@@ -668,6 +736,9 @@ void cloth_rollout_destroy(ClothRollout *ro)
     cudaFree(ro->ckpt);
     cudaFree(ro->seg);
     cudaFree(ro->cbits);
+    if (ro->side) cudaStreamDestroy(ro->side);
+    for (cudaEvent_t ev : {ro->ev_fork, ro->ev_join, ro->ev_rec[0], ro->ev_rec[1], ro->ev_rev[0], ro->ev_rev[1]})
+        if (ev) cudaEventDestroy(ev);
     cudaFree(ro->lam);
     cudaFree(ro->gslot);
     cudaFree(ro->final_state);
