@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched, adjoint and atomic A/B legs")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the e2e leg (default: --steps, max 1000)")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint leg and print its result (for profiling the rollout)")
     return ap.parse_args()
 
 
@@ -595,6 +597,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjoint_only:
+        import torch
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            print(json.dumps({"adjoint": run_adjoint(stream)}), flush=True)
+        return 0
     return run_ours(args)
 
 
