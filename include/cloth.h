@@ -288,9 +288,14 @@ void cloth_batch_destroy(ClothBatch *b);
  * forward pass finds (the response is differentiated as a smooth map of the
  * start point and the path direction).  The forward pass stores the state
  * every checkpoint_every steps; the backward pass recomputes one segment at
- * a time, so device memory grows as nsteps/checkpoint_every + checkpoint_every
- * copies of the state.  All pointers below are device pointers on the
- * cloth's device; all calls run on the cloth's stream. */
+ * a time into one of two slot sets while the previous segment is reversed,
+ * so device memory grows as nsteps/checkpoint_every states plus
+ * 2 x (checkpoint_every x substeps + 1) slots of 19 planes.  The forward and
+ * backward passes run as CUDA graphs captured on first use (rebuilt after
+ * cloth_set_mesh) unless the cloth has CLOTH_FLAG_NO_GRAPH; the backward
+ * pass also uses a stream of the rollout's own, joined to the cloth's stream
+ * before the call's last work.  All pointers below are device pointers on
+ * the cloth's device; all calls run on the cloth's stream. */
 typedef struct ClothRollout ClothRollout;
 
 /* The cloth's current state (at its current substep count) becomes the

@@ -3,14 +3,16 @@
 // velocities, with the contact set of every substep frozen at the one the
 // forward pass found.  A rollout runs the forward pass keeping a checkpoint
 // every `checkpoint_every` steps; the backward pass recomputes one segment at
-// a time (storing each substep's start state and post-integration velocity)
-// and walks it in reverse:
+// a time (storing each substep's start state, post-integration velocity and
+// the response data of the nodes that hit) and walks it in reverse, the
+// recompute of the next segment overlapping the reverse of the current one:
 //   response   x' = S + m r (contact: m = mean max(t_k - delta, 0) over the
 //              hits, r = v*/|v*|, v' = c v*) or x' = S + dt v*, v' = v*;
 //   Euler      v* = v + dt (F/m + g + w);
 //   springs    Algorithm 1's force, differentiated in x, v, ks, kd; each node
-//              gathers its twelve springs, each spring's owner alone writes
-//              its ks/kd gradient (no atomics, fixed order).
+//              gathers its twelve springs (four lanes, three each), each
+//              spring's owner alone writes its ks/kd gradient (no atomics,
+//              fixed order).
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>

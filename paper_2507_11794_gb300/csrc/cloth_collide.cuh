@@ -1,5 +1,5 @@
 // Collision of a node's substep path with the surface model (device code
-// shared by the forward and the reverse pass).
+// shared by the stepping kernels and the adjoint's recompute).
 //
 // Broad phase (Section 4.3): the path S -> E is boxed and the triangles
 // listed in the grid cells of that box are the candidates; a triangle listed
@@ -84,11 +84,12 @@ __device__ __forceinline__ bool coll_path(const StepParams &p, float sx, float s
 
 // Broad + narrow phase and response of one node, one thread walking all
 // candidates in (z, y, x) cell order and entry order.  On K > 0 hits returns
-// true and the response position.  GRAD also returns, for the reverse pass,
-// mK = (m, K, r) with m = mean max(t_k - delta, 0), and over the active hits
-// (t_k > delta) the sums g1 = sum n/a and g2 = sum t n/a (n = e1 x e2), the
-// derivatives of t_k w.r.t. S and r.  The cooperative forward kernel below
-// sums the same hits in the same order, so both see the same response.
+// true and the response position.  GRAD also returns, for the adjoint's
+// recompute of an over-long path, mK = (m, K, r) with
+// m = mean max(t_k - delta, 0), and over the active hits (t_k > delta) the
+// sums g1 = sum n/a and g2 = sum t n/a (n = e1 x e2), the derivatives of t_k
+// w.r.t. S and r.  The cooperative kernel below sums the same hits in the
+// same order, so both see the same response.
 template <bool GRAD>
 __device__ __forceinline__ bool collide_t(const StepParams &p, float sx, float sy, float sz, float ex, float ey,
                                           float ez, float &ox, float &oy, float &oz, float *g1 = nullptr,
