@@ -41,20 +41,22 @@ __global__ void __launch_bounds__(NB_COLS) normals_kernel(const float *__restric
             const unsigned o = (unsigned)rr * (unsigned)pitch + (unsigned)cc;
             return V3{__ldg(px + o), __ldg(py + o), __ldg(pz + o)};
         };
-        const V3 v = P(r, c);
         const bool up = r >= 1, down = r + 1 < ny, left = c >= 1, right = c + 1 < nx;
+        // all seven points are loaded unconditionally (clamped into the grid)
+        // so their loads overlap; the branches below only select the faces
+        const int ru = up ? r - 1 : r, rd = down ? r + 1 : r, cl = left ? c - 1 : c, cr = right ? c + 1 : c;
+        const V3 v = P(r, c), d = P(rd, c), e = P(rd, cr), b = P(r, cr), u = P(ru, c), l = P(r, cl),
+                 a = P(ru, cl);
         V3 n = {0.0f, 0.0f, 0.0f};
         if (down && right) {  // quad (r, c): both triangles
-            const V3 d = P(r + 1, c), e = P(r + 1, c + 1), b = P(r, c + 1);
             add_face(n, v, d, e);
             add_face(n, v, e, b);
         }
-        if (up && right) add_face(n, P(r - 1, c), v, P(r, c + 1));    // quad (r-1, c), first triangle
-        if (down && left) add_face(n, P(r, c - 1), P(r + 1, c), v);   // quad (r, c-1), second triangle
-        if (up && left) {                                              // quad (r-1, c-1): both
-            const V3 a = P(r - 1, c - 1);
-            add_face(n, a, P(r, c - 1), v);
-            add_face(n, a, v, P(r - 1, c));
+        if (up && right) add_face(n, u, v, b);    // quad (r-1, c), first triangle
+        if (down && left) add_face(n, l, d, v);   // quad (r, c-1), second triangle
+        if (up && left) {                         // quad (r-1, c-1): both
+            add_face(n, a, l, v);
+            add_face(n, a, v, u);
         }
         const float l2 = n.x * n.x + n.y * n.y + n.z * n.z;
         const float s = l2 > 0.0f ? 1.0f / sqrtf(l2) : 0.0f;

@@ -533,6 +533,13 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kern
     }
     __syncthreads();
     const unsigned long long k = s_k;
+    if (s_n == 0u) {
+        // nothing listed (every CTA sees the same final count): CTA 0 alone
+        // ends the substep; the others read k only to ignore it, and the
+        // next kernel reads it after this grid completes
+        if (blockIdx.x == 0 && threadIdx.x == 0) p.ctrl->k = k + 1;
+        return;
+    }
     float fsum = 0.0f;
     collide_list<REC>(OneClothList{p}, sh, k, s_n, fsum);
     if (__any_sync(FULL, !isfinite(fsum)) && (threadIdx.x & 31) == 0)
