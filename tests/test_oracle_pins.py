@@ -293,6 +293,91 @@ def test_mt_constructed_hits_and_misses(oracle_lib):
     assert nhit > 300 and nmiss > 1000
 
 
+def _det3(a, b, c):
+    return (a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0])
+            + a[2] * (b[0] * c[1] - b[1] * c[0]))
+
+
+def test_mt_matches_exact_rational_segment_triangle_intersection(oracle_lib):
+    # Ground truth in exact rational arithmetic from the definition: solve
+    # S + s d = V0 + u e1 + v e2 (d = E - S) by Cramer's rule and apply the
+    # test's conditions (reading C6): |a| >= eps with a = r . (e2 x e1),
+    # r = d/|d|, i.e. (d . (e1 x e2))^2 >= eps^2 |d|^2; u in [0, 1], v >= 0,
+    # u + v <= 1; t = s |d| in (eps, |d|).  Squares keep |d| out of it, so
+    # everything stays rational.  Pairs within 1e-9 of a threshold are
+    # skipped (away from ties, where double rounding may decide either way).
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(23)
+    eps = 1e-7
+    fe = Fr(eps)
+    nhit = nmiss = nskip = 0
+    reasons = set()
+    for it in range(10000):
+        V = rng.normal(0, 1, (3, 3))
+        e1, e2 = V[1] - V[0], V[2] - V[0]
+        u0, v0 = rng.uniform(-0.3, 1.3, 2)
+        P = V[0] + u0 * e1 + v0 * e2
+        kind = it % 4
+        r = rng.normal(0, 1, 3)
+        if kind == 1:  # nearly parallel to the triangle's plane
+            n = np.cross(e1, e2)
+            n /= np.linalg.norm(n)
+            r = r - np.dot(r, n) * n + rng.choice([1e-12, 1e-9, 1e-6, 1e-3]) * n
+        r /= np.linalg.norm(r)
+        t0 = rng.uniform(-0.5, 1.5) if kind != 2 else rng.choice([1e-9, 5e-8, 2e-7, 1e-6])
+        L = rng.uniform(0.05, 2.0)
+        S = P - t0 * r
+        E = S + L * r
+        # exact decision
+        FS, FE = [Fr(float(x)) for x in S], [Fr(float(x)) for x in E]
+        FV = [[Fr(float(x)) for x in row] for row in V]
+        d = [FE[k] - FS[k] for k in range(3)]
+        f1 = [FV[1][k] - FV[0][k] for k in range(3)]
+        f2 = [FV[2][k] - FV[0][k] for k in range(3)]
+        b = [FV[0][k] - FS[k] for k in range(3)]
+        m1 = [-x for x in f1]
+        m2 = [-x for x in f2]
+        L2 = sum(x * x for x in d)
+        det = _det3(d, m1, m2)
+        margins = []
+        if det == 0:
+            exact_hit, why = False, "parallel"
+        else:
+            par = det * det - fe * fe * L2  # |a| >= eps  <=>  par >= 0
+            sc = _det3(b, m1, m2) / det
+            u = _det3(d, b, m2) / det
+            v = _det3(d, m1, b) / det
+            tl = sc * sc * L2 - fe * fe  # t > eps  <=>  s > 0 and tl > 0
+            margins = [float(par) / max(float(fe * fe * L2), 1e-300), float(u), float(1 - u), float(v),
+                       float(1 - u - v), float(sc - 1), float(sc)]
+            if float(L2) > 0:
+                margins.append(float(tl) / float(fe * fe))
+            if par < 0:
+                exact_hit, why = False, "parallel"
+            elif not (0 <= u <= 1 and v >= 0 and u + v <= 1):
+                exact_hit, why = False, "outside"
+            elif not (sc > 0 and tl > 0):
+                exact_hit, why = False, "behind or within eps"
+            elif not sc < 1:
+                exact_hit, why = False, "beyond the end"
+            else:
+                exact_hit, why = True, "hit"
+        if any(abs(m) < 1e-9 for m in margins):
+            nskip += 1
+            continue
+        got = oracle_lib.mt(S, E, V[0], V[1], V[2], eps)
+        assert (got is not None) == exact_hit, (it, why, got)
+        reasons.add(why)
+        if exact_hit:
+            t_exact = float(sc) * float(np.sqrt(float(L2)))
+            assert got == pytest.approx(t_exact, rel=1e-8, abs=1e-12)
+            nhit += 1
+        else:
+            nmiss += 1
+    assert nhit > 500 and nmiss > 5000 and nskip < 500, (nhit, nmiss, nskip)
+    assert reasons == {"hit", "parallel", "outside", "behind or within eps", "beyond the end"}
+
+
 # ------------------------------------------------------------ response (Alg. 2)
 
 @pytest.mark.parametrize("name,vals", _golden("response_cases.txt"))
