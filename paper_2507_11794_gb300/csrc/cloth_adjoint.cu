@@ -679,8 +679,9 @@ int cloth_rollout_forward(ClothRollout *ro, const float *d_ks, const float *d_kd
     if (h->dead) return rfail(CLOTH_ERR_STATE, "handle unusable after an earlier CUDA error");
     const long long st = h->stride;
     cudaStream_t s = h->stream;
-    if (d_ks) scatter_kernel<<<nblk(ro->S, 256), 256, 0, s>>>(d_ks, ro->map, ro->S, h->ks_slot);
-    if (d_kd) scatter_kernel<<<nblk(ro->S, 256), 256, 0, s>>>(d_kd, ro->map, ro->S, h->kd_slot);
+    // a cloth of one row and one column has no springs (S = 0): nothing to scatter or gather
+    if (d_ks && ro->S > 0) scatter_kernel<<<nblk(ro->S, 256), 256, 0, s>>>(d_ks, ro->map, ro->S, h->ks_slot);
+    if (d_kd && ro->S > 0) scatter_kernel<<<nblk(ro->S, 256), 256, 0, s>>>(d_kd, ro->map, ro->S, h->kd_slot);
     RTRY(h, cudaGetLastError(), "constants scatter");
     ro->kseg[0] = ro->k0;
     RTRY(h, cudaMemcpyAsync(&h->ctrl->k, &ro->kseg[0], sizeof(unsigned long long), cudaMemcpyHostToDevice, s),
@@ -716,8 +717,9 @@ int cloth_rollout_backward(ClothRollout *ro, const float *d_gpos, const float *d
     RTRY(h, cudaGetLastError(), "load output adjoints");
     RTRY(h, run_pass(ro, true, s), "reverse pass");
     if (d_gv0) planes_aos_kernel<<<nblk(n, 256), 256, 0, s>>>(lv, n, nx, h->pitch, st, d_gv0);
-    if (d_gks) gather_kernel<<<nblk(ro->S, 256), 256, 0, s>>>(ro->gslot, ro->map, ro->S, d_gks);
-    if (d_gkd) gather_kernel<<<nblk(ro->S, 256), 256, 0, s>>>(ro->gslot + 6 * st, ro->map, ro->S, d_gkd);
+    if (d_gks && ro->S > 0) gather_kernel<<<nblk(ro->S, 256), 256, 0, s>>>(ro->gslot, ro->map, ro->S, d_gks);
+    if (d_gkd && ro->S > 0)
+        gather_kernel<<<nblk(ro->S, 256), 256, 0, s>>>(ro->gslot + 6 * st, ro->map, ro->S, d_gkd);
     RTRY(h, cudaGetLastError(), "gradient outputs");
     // leave the cloth in its final forward state
     RTRY(h, cudaMemcpyAsync(&h->ctrl->k, &ro->k_final, sizeof(unsigned long long), cudaMemcpyHostToDevice, s),

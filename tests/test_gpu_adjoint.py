@@ -279,3 +279,32 @@ def test_rollout_follows_a_mesh_change(cloth_lib):
     assert not np.array_equal(a[0][3], a[1][3])  # the contact changed the result
     for u, w in zip(a[1], b[0]):
         assert np.array_equal(u, w)
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (2, 1), (1, 3), (3, 2)])
+def test_rollout_on_minimal_cloths(cloth_lib, oracle_lib, nx, ny):
+    # Cloths with no springs (1x1), only structural ones (1x3) and the smallest
+    # with shear springs, falling onto the floor: the GPU gradients match the
+    # FP64 adjoint (contact bound as above); a spring-less cloth returns empty
+    # per-spring gradients.
+    rng = np.random.default_rng(15 + nx * 7 + ny)
+    n = nx * ny
+    vel = np.zeros((n, 3))
+    vel[:, 1] = -0.6
+    vel += rng.normal(0, 0.05, vel.shape)
+    sc = make_scene(nx, ny, origin=(0.3, 0.0015, 0.3), du=(0.05, 0, 0), dv=(0, 0, 0.05), total_mass=0.2,
+                    gravity=(0, -9.81, 0), dt=2e-3, substeps=4, vel=vel, mesh=floor_mesh(), delta=1e-4)
+    S = cs.spring_count(nx, ny)
+    sc.ks_spring = rng.uniform(20, 40, S).astype(np.float32)
+    sc.kd_spring = rng.uniform(0.01, 0.05, S).astype(np.float32)
+    v0 = sc.init_vel.astype(np.float32)
+    tgt = sc.init_pos + rng.normal(0, 0.01, sc.init_pos.shape)
+    gks, gkd, gv0, pos = _gpu_grads(cloth_lib, sc, sc.ks_spring, sc.kd_spring, v0, tgt, 8, 3)
+    oks, okd, ov0, x = _oracle_grads(oracle_lib, sc, sc.ks_spring.astype(np.float64),
+                                     sc.kd_spring.astype(np.float64), v0.astype(np.float64), tgt, 8,
+                                     oracle_lib.Grid(*floor_mesh()))
+    assert np.max(np.abs(pos - x)) < 1e-5
+    assert gks.shape == (S,) and gkd.shape == (S,)
+    pairs = [(gv0, ov0)] + ([(gks, oks), (gkd, okd)] if S else [])
+    for got, ref in pairs:
+        assert _l2(got, ref) <= 2e-3
