@@ -136,3 +136,25 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(A, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         A.lib()
+
+
+@pytest.mark.parametrize("nx,ny,what", [(1, 1 << 30, b"plane"), (1 << 16, 1 << 15, b"too many nodes")])
+def test_create_rejects_the_largest_grids_without_gpu(capi, nx, ny, what):
+    # kernels index a plane with 32-bit offsets: a padded plane of 2^31 floats
+    # or more, or more than 2^30 nodes, is refused before any allocation
+    d = _desc(capi, nx=nx, ny=ny)
+    h = C.c_void_p()
+    assert capi.lib().cloth_create(C.byref(d), None, C.byref(h)) == capi.CLOTH_ERR_INVALID_ARG
+    assert h.value is None
+    assert what in capi.lib().cloth_last_error()
+
+
+def test_rollout_entry_points_reject_null_arguments(capi):
+    L = capi.lib()
+    r = C.c_void_p()
+    assert L.cloth_rollout_create(None, 8, 2, C.byref(r)) == capi.CLOTH_ERR_INVALID_ARG
+    assert r.value is None
+    assert L.cloth_rollout_create(None, 8, 2, None) == capi.CLOTH_ERR_INVALID_ARG
+    assert L.cloth_rollout_forward(None, None, None, None, None, None) == capi.CLOTH_ERR_INVALID_ARG
+    assert L.cloth_rollout_backward(None, None, None, None, None, None) == capi.CLOTH_ERR_INVALID_ARG
+    L.cloth_rollout_destroy(None)  # NULL-safe
