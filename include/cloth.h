@@ -220,7 +220,7 @@ int cloth_query_candidates(ClothHandle *h, const float *S, const float *E, int32
  * launches run back to back), and report the mean device
  * duration per launch in microseconds: walk_us for the force + integration
  * kernel (Algorithm 1 and Section 3), collide_us for the collision kernel
- * (Section 4.3 and Algorithm 2; 0 without a surface model).  The state
+ * (Section 3 and Algorithm 2; 0 without a surface model).  The state
  * advances exactly as with cloth_step.  nsub in [1, 4096]; either output may
  * be NULL.  Synchronises.  Errors: CLOTH_ERR_INVALID_ARG, CLOTH_ERR_CUDA,
  * and the flag errors of cloth_sync. */
@@ -337,12 +337,14 @@ typedef struct ClothGridParams {
 
 /* The paper has no counterpart to this entry point: it is a variant of the
  * grid build inside cloth_set_mesh for callers that must not allocate device
- * memory -- code that runs while a CUDA graph is being captured, inside
- * another library's stream-ordered region, or under an allocator with a fixed
- * budget or a ban on cudaMalloc/cudaFree after start-up.  It allocates
- * nothing: its temporaries live in one fixed-size device array of the library
- * (7,341,312 bytes, held on every GPU that loads the library until the
- * process exits), and the caller supplies the outputs.
+ * memory -- hosts that run under an allocator with a fixed budget, or that
+ * forbid cudaMalloc/cudaFree once start-up is over.  It calls no allocating
+ * routine: its temporaries live in one fixed-size device array of the library
+ * (7,341,312 bytes), and the caller supplies the outputs.  A device holds that
+ * array from the moment the library's module is loaded on it until the
+ * process exits; with CUDA's lazy module loading (the default) the load can
+ * happen at the first call on that device, so a caller that may not allocate
+ * later makes one call per device during start-up.
  *
  * Inputs: host arrays verts [nverts][3] float32 and tris [ntris][3] int32
  * (the same mesh cloth_set_mesh takes), at most CLOTH_STATIC_GRID_MAX_TRIS
@@ -367,8 +369,9 @@ typedef struct ClothGridParams {
  * device) race on the scratch and give wrong results: serialise them.  The
  * first call on each device looks the array's device address up (with that
  * device current) and should come before any stream capture on that device.
- * Errors: CLOTH_ERR_INVALID_ARG, CLOTH_ERR_BAD_MESH (index out of range,
- * non-finite vertex), CLOTH_ERR_CUDA. */
+ * Errors: CLOTH_ERR_INVALID_ARG (limits, capacities, a device index of 64 or
+ * more), CLOTH_ERR_BAD_MESH (index out of range, non-finite vertex, 2^31 - 1
+ * or more (cell, triangle) pairs), CLOTH_ERR_CUDA. */
 int cloth_grid_build_static(const float *verts, int32_t nverts, const int32_t *tris, int32_t ntris, void *stream,
                             float *d_tri_records, int32_t *d_cell_start, int64_t cell_capacity,
                             int32_t *d_tri_ids, int64_t entry_capacity, ClothGridParams *params);

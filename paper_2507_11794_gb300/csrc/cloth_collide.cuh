@@ -1,11 +1,12 @@
 // Collision of a node's substep path with the surface model (device code
 // shared by the stepping kernels and the adjoint's recompute).
 //
-// Broad phase (Section 4.3): the path S -> E is boxed and the triangles
-// listed in the grid cells of that box are the candidates; a triangle listed
-// in several of those cells is tested only in the first cell the two boxes
-// share.  Narrow phase: the extended Moller-Trumbore test (Algorithm 1) of the
-// path against each candidate.  Response (Algorithm 2): with K hits at
+// Broad phase (not in the paper, which tests every pair; a uniform grid over
+// the surface triangles): the path S -> E is boxed and the triangles listed in
+// the grid cells of that box are the candidates; a triangle listed in several
+// of those cells is tested only in the first cell the two boxes share.
+// Narrow phase: the extended Moller-Trumbore test of Section 3 on the path
+// against each candidate.  Response (Algorithm 2): with K hits at
 // distances t_k along r = (E - S)/|E - S|, the node moves to
 // S + mean_k max(t_k - delta, 0) r and its velocity is scaled by the
 // restitution factor.

@@ -376,8 +376,9 @@ cudaError_t grid_query(const DevGrid &g, const float *dS, const float *dE, int n
 
 // Grid build with every temporary buffer supplied by the caller (no
 // allocation).  Same kernels and order as grid_build.  Writes the pair count
-// to *nentries after the counting pass; when it exceeds entry_cap nothing
-// more is written and *done is false.  Synchronises s.
+// to *nentries after the counting pass; when it exceeds entry_cap, or int32
+// offsets (2^31 - 1 or more), nothing more is written and *done is false.
+// Synchronises s.
 cudaError_t grid_build_noalloc(const float *d_verts, const int *d_tris, int nt, const float origin[3], float inv,
                                const int dims[3], float4 *rec, int *cell_start, int *tri_ids, long long entry_cap,
                                int4 *box_hi, unsigned *cnt, unsigned *cursor, unsigned *sums,
@@ -397,7 +398,8 @@ cudaError_t grid_build_noalloc(const float *d_verts, const int *d_tris, int nt, 
     if ((e = cudaMemcpyAsync(&htotal, total, sizeof(htotal), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     *nentries = (long long)htotal;
-    if ((long long)htotal > entry_cap) return cudaSuccess;
+    // too many pairs for the caller's buffer, or for int32 cell offsets
+    if ((long long)htotal > entry_cap || htotal >= 0x7fffffffull) return cudaSuccess;
     cell_count_kernel<<<blocks_for(nt, 256), 256, 0, s>>>(rec, box_hi, nt, dims[0], dims[1], cnt);
     scan_reduce_kernel<<<(int)ntiles, SCAN_THREADS, 0, s>>>(cnt, nc, sums);
     scan_sums_kernel<<<1, SCAN_THREADS, 0, s>>>(sums, ntiles);

@@ -1,9 +1,9 @@
 // cloth_grid_build_static: the uniform-grid build of cloth_set_mesh for
-// callers that cannot allocate device memory -- code running inside a CUDA
-// graph capture or another library's stream-ordered region, allocators with a
-// fixed budget, or hosts that forbid cudaMalloc/cudaFree after start-up.  All
-// temporaries live in one file-scope device array of fixed size, so this entry
-// point allocates nothing; the caller supplies the output buffers.
+// callers that cannot allocate device memory -- hosts that run under an
+// allocator with a fixed budget, or that forbid cudaMalloc/cudaFree once
+// start-up is over.  All temporaries live in one file-scope device array of
+// fixed size, so this entry point allocates nothing; the caller supplies the
+// output buffers.
 #include <math.h>
 #include <stdarg.h>
 #include <stdint.h>
@@ -31,7 +31,9 @@ constexpr size_t kOffSums = align256(kOffCursor + sizeof(unsigned) * kMaxCells);
 constexpr size_t kOffTotal = align256(kOffSums + sizeof(unsigned) * kTiles);
 constexpr size_t kScratchBytes = align256(kOffTotal + sizeof(unsigned long long));
 
-// Every GPU that loads the library holds this array until the process exits.
+// A device holds this array from the moment the library's module is loaded on
+// it (with CUDA's lazy module loading, at the first use of the library on that
+// device, which may be the first call below) until the process exits.
 static __device__ __align__(256) unsigned char g_grid_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -100,8 +102,10 @@ extern "C" int cloth_grid_build_static(const float *verts, int32_t nverts, const
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return fail(CLOTH_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(CLOTH_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(CLOTH_ERR_INVALID_ARG, "device %d: the static grid build serves devices 0..%d", dev,
+                    kMaxDevices - 1);
     unsigned char *base = nullptr;
     if ((e = scratch_address(dev, &base)) != cudaSuccess)
         return fail(CLOTH_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
@@ -120,6 +124,9 @@ extern "C" int cloth_grid_build_static(const float *verts, int32_t nverts, const
                                s);
         if (e == cudaSuccess) {
             params->nentries = nent;
+            if (nent >= 0x7fffffffLL)  // cell_start and tri_ids are int32
+                return fail(CLOTH_ERR_BAD_MESH, "%lld (cell, triangle) pairs: more than int32 indices address",
+                            nent);
             if (!done)
                 return fail(CLOTH_ERR_INVALID_ARG, "d_tri_ids holds %lld ints, needs %lld",
                             (long long)entry_capacity, nent);

@@ -158,3 +158,40 @@ def test_rollout_entry_points_reject_null_arguments(capi):
     assert L.cloth_rollout_forward(None, None, None, None, None, None) == capi.CLOTH_ERR_INVALID_ARG
     assert L.cloth_rollout_backward(None, None, None, None, None, None) == capi.CLOTH_ERR_INVALID_ARG
     L.cloth_rollout_destroy(None)  # NULL-safe
+
+
+def _static_reject(capi, verts, tris):
+    # limits are checked on the host before any CUDA call (no GPU needed)
+    rc, prm = capi.cloth_grid_build_static(verts, tris, 0, 0, 0, 0, 0, 0)
+    return rc, prm, capi.lib().cloth_last_error()
+
+
+def test_static_grid_rejects_too_many_vertices_alone(capi):
+    import numpy as np
+    nv = 131073  # one over the vertex limit, with a single triangle
+    verts = np.zeros((nv, 3), np.float32)
+    verts[1, 0] = verts[2, 1] = 1.0
+    tris = np.array([[0, 1, 2]], np.int32)
+    rc, _, msg = _static_reject(capi, verts, tris)
+    assert rc == capi.CLOTH_ERR_INVALID_ARG and b"static limits" in msg and b"131073 vertices" in msg
+
+
+def test_static_grid_rejects_too_many_triangles_alone(capi):
+    import numpy as np
+    nt = 131073
+    verts = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    tris = np.tile(np.array([0, 1, 2], np.int32), (nt, 1))
+    rc, _, msg = _static_reject(capi, verts, tris)
+    assert rc == capi.CLOTH_ERR_INVALID_ARG and b"131073 triangles" in msg
+
+
+def test_static_grid_rejects_a_grid_over_the_cell_limit(capi):
+    import numpy as np
+    # two triangles of side 5 mm at opposite corners of a unit cube: the cell
+    # is twice the mean longest side (1 cm), so the grid has about 104^3 cells
+    s = 0.005
+    verts = np.array([[0, 0, 0], [s, 0, 0], [0, s, 0], [1, 1, 1], [1 - s, 1, 1], [1, 1 - s, 1]], np.float32)
+    tris = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+    rc, prm, msg = _static_reject(capi, verts, tris)
+    assert rc == capi.CLOTH_ERR_INVALID_ARG and b"cells exceeds the static limit" in msg
+    assert prm.ncells > 262144 and prm.ncells == prm.dims[0] * prm.dims[1] * prm.dims[2]
