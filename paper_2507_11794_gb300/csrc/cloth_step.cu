@@ -72,7 +72,17 @@ __device__ __forceinline__ void pdl_launch_dependents()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 #endif
 }
-constexpr int WARPS_PER_CTA = 4;
+#ifndef CLOTH_WALK_WARPS
+#define CLOTH_WALK_WARPS 4
+#endif
+constexpr int WARPS_PER_CTA = CLOTH_WALK_WARPS;
+// register budget of the walk kernels: CLOTH_WALK_MAXREG registers per thread
+// when given, else what CLOTH_WALK_MINB resident CTAs per SM leave
+#ifdef CLOTH_WALK_MAXREG
+#define CLOTH_WALK_BOUNDS __maxnreg__(CLOTH_WALK_MAXREG)
+#else
+#define CLOTH_WALK_BOUNDS __launch_bounds__(32 * CLOTH_WALK_WARPS, CLOTH_WALK_MINB)
+#endif
 constexpr int STRIP_COLS = 60;
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -109,22 +119,21 @@ __device__ __forceinline__ Planes planes(float *base, long long st)
     return {{base, base + st, base + 2 * st, base + 3 * st, base + 4 * st, base + 5 * st}};
 }
 
-// Row r of the lane's two columns (zeros outside the grid's rows / memory);
-// o = r * pitch + cA is a 32-bit plane offset.
-__device__ __forceinline__ Node2 load_row(const Planes &in, int r, int ny, int pitch, int cA, bool colmem)
+// Row r of the lane's two columns.  The row and the column pair are clamped
+// into the grid's memory, so every load is in bounds; the values of a row
+// outside [0, ny) or a pair outside the pitch are finite stand-ins that only
+// enter springs whose constants are zero (no spring there).
+__device__ __forceinline__ Node2 load_row(const Planes &in, int r, int ny, int pitch, int cmem)
 {
+    const int rr = min(max(r, 0), ny - 1);
+    const unsigned o = (unsigned)rr * (unsigned)pitch + (unsigned)cmem;
     Node2 n;
-    if (r >= 0 && r < ny && colmem) {
-        const unsigned o = (unsigned)r * (unsigned)pitch + (unsigned)cA;
-        n.px = __ldg((const float2 *)(in.k[0] + o));
-        n.py = __ldg((const float2 *)(in.k[1] + o));
-        n.pz = __ldg((const float2 *)(in.k[2] + o));
-        n.vx = __ldg((const float2 *)(in.k[3] + o));
-        n.vy = __ldg((const float2 *)(in.k[4] + o));
-        n.vz = __ldg((const float2 *)(in.k[5] + o));
-    } else {
-        n.px = n.py = n.pz = n.vx = n.vy = n.vz = make_float2(0.0f, 0.0f);
-    }
+    n.px = __ldg((const float2 *)(in.k[0] + o));
+    n.py = __ldg((const float2 *)(in.k[1] + o));
+    n.pz = __ldg((const float2 *)(in.k[2] + o));
+    n.vx = __ldg((const float2 *)(in.k[3] + o));
+    n.vy = __ldg((const float2 *)(in.k[4] + o));
+    n.vz = __ldg((const float2 *)(in.k[5] + o));
     return n;
 }
 
@@ -145,18 +154,28 @@ __device__ __forceinline__ Vec2 spring2(const Node2 &P, const Node2 &Q, float2 k
     return {mul2(sc, dx), mul2(sc, dy), mul2(sc, dz)};
 }
 
+__device__ __forceinline__ Vec2 vscale(Vec2 a, float2 s) { return {mul2(a.x, s), mul2(a.y, s), mul2(a.z, s)}; }
+
+// Per-lane spring constants of a strip: the type's ks, kd where the spring
+// exists for the lane's columns (both ends inside the grid), else zero.
+struct LaneK {
+    float2 ksR, kdR, ksR2, kdR2, ksD, kdD, ksD2, kdD2, ksDR, kdDR, ksDL, kdDL;
+};
+
 // One warp's strip: columns [60 sx - 2, 60 sx + 62) walked down rows
 // [r0 - 2, r0 + rows_per_warp) with a register window of rows r .. r+2 (row
 // r+3 in flight).  Lane l holds the pair of columns (cA, cA + 1),
 // cA = 60 sx - 2 + 2 l, and evaluates the six springs its two nodes own
 // (Algorithm 1; the forward directions (0,+1), (0,+2), (+1,0), (+2,0),
 // (+1,+1), (+1,-1)); the reaction of each spring reaches the other end
-// through a shuffle (same row) or a register carried to the next row.  Rows
-// r0 - 2 and r0 - 1 are the halo: they evaluate only the springs that end in
-// row r0 or r0 + 1.  Then symplectic Euler with gravity, wind and pins
-// (Section 3) writes rows [r0, r1) of the output state and, with a surface
-// model, the nodes whose path box reaches the grid's inner cells are appended
-// to the collision list.
+// through a shuffle (same row) or through the running sum of the reactions
+// that the rows above send into the next row.  Rows r0 - 2 and r0 - 1 are the
+// halo: they evaluate only the springs that end in row r0 or r0 + 1.  Then
+// symplectic Euler with gravity, wind and pins (Section 3) writes rows
+// [r0, r1) of the output state and, with a surface model, the nodes whose
+// path box reaches the grid's inner cells are appended to the collision list.
+// The row loop is unrolled four times with the window's four row slots
+// renamed at each step, so the window moves without register copies.
 template <bool MESH, bool PER_SPRING>
 __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__restrict__ in, float *__restrict__ out,
                                            float wbase, int sx, int sy, int lane, int cloth,
@@ -168,11 +187,31 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
     const int r0 = sy * p.rows_per_warp;
     const int r1 = min(r0 + p.rows_per_warp, p.ny);  // output rows [r0, r1)
     const bool colmem = cA >= 0 && cA < p.pitch;     // both columns addressable
+    const int cmem = min(max(cA, 0), p.pitch - 2);   // the pair loaded (clamped)
     const bool out_lane = lane >= 1 && lane <= 30;
     auto colok = [&](int c) { return c >= 0 && c < p.nx; };
     const bool okA = out_lane && colok(cA), okB = out_lane && colok(cA + 1);
-    // every lane's columns cA-1 .. cA+3 inside the grid
-    const bool colint = sx * STRIP_COLS - 3 >= 0 && sx * STRIP_COLS + 64 < p.nx;
+
+    LaneK K;
+    if (!PER_SPRING) {
+        // a spring exists when both ends are grid nodes (A in .x, B in .y)
+        const float2 mR = make_float2(colok(cA) && colok(cA + 1), colok(cA + 1) && colok(cA + 2));
+        const float2 mR2 = make_float2(colok(cA) && colok(cA + 2), colok(cA + 1) && colok(cA + 3));
+        const float2 mD = make_float2(colok(cA), colok(cA + 1));
+        const float2 mDL = make_float2(colok(cA) && colok(cA - 1), colok(cA + 1) && colok(cA));
+        K.ksR = mul2(mR, bc(p.ks[0]));
+        K.kdR = mul2(mR, bc(p.kd[0]));
+        K.ksD = mul2(mD, bc(p.ks[0]));
+        K.kdD = mul2(mD, bc(p.kd[0]));
+        K.ksDR = mul2(mR, bc(p.ks[1]));
+        K.kdDR = mul2(mR, bc(p.kd[1]));
+        K.ksDL = mul2(mDL, bc(p.ks[1]));
+        K.kdDL = mul2(mDL, bc(p.kd[1]));
+        K.ksR2 = mul2(mR2, bc(p.ks[2]));
+        K.kdR2 = mul2(mR2, bc(p.kd[2]));
+        K.ksD2 = mul2(mD, bc(p.ks[2]));
+        K.kdD2 = mul2(mD, bc(p.kd[2]));
+    }
 
     // wind: sin(base + alpha_r + beta_c) from per-row and per-column tables of
     // (sin, cos) and the addition formula; depends only on (row, col, time)
@@ -208,21 +247,25 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
     row_inputs(r0, trN, pinN);
 
     int r = r0 - 2;
-    Node2 P0 = load_row(pin, r, p.ny, p.pitch, cA, colmem);
-    Node2 P1 = load_row(pin, r + 1, p.ny, p.pitch, cA, colmem);
-    Node2 P2 = load_row(pin, r + 2, p.ny, p.pitch, cA, colmem);
-    Node2 N0{};  // lane+1's pair, row r (from row r0 on)
-    // carried spring forces (owner's forward spring; the reaction is subtracted)
-    Vec2 fD_1 = {}, fD2_1 = {}, fD2_2 = {};  // own down (r-1), down2 (r-1), down2 (r-2)
-    Vec2 bDR_1 = {}, bDL_1 = {};             // reactions of the diagonals of row r-1
+    // the window's four row slots and the two slots of lane+1's pair
+    Node2 Pa = load_row(pin, r, p.ny, p.pitch, cmem);
+    Node2 Pb = load_row(pin, r + 1, p.ny, p.pitch, cmem);
+    Node2 Pc = load_row(pin, r + 2, p.ny, p.pitch, cmem);
+    Node2 Pd, Ne, Nf;
+    // reactions sent into the next row by the rows above (springs (+1,0),
+    // (+1,+1), (+1,-1) of row r-1 and (+2,0) of row r-2), and the (+2,0)
+    // reactions of row r-1 (they reach row r+1)
+    Vec2 A1 = {}, D2p = {};
     unsigned long long markA = 0ull, markB = 0ull;  // rows whose node needs the collision phase
 
     // PH 0: row r0-2 (only its (+2,0) spring reaches an output row);
-    // PH 1: row r0-1 (its (+1,*) and (+2,0) springs); PH 2: output rows
-    auto row = [&](auto phase) {
+    // PH 1: row r0-1 (its (+1,*) and (+2,0) springs); PH 2: output rows.
+    // P0, P1, P2: rows r, r+1, r+2; P3 receives row r+3; N0: lane+1's pair of
+    // row r (from the previous row); N1 receives lane+1's pair of row r+1.
+    auto row = [&](auto phase, Node2 &P0, Node2 &P1, Node2 &P2, Node2 &P3, Node2 &N0, Node2 &N1) {
         constexpr int PH = decltype(phase)::value;
-        const Node2 P3 = load_row(pin, r + 3, p.ny, p.pitch, cA, colmem);  // prefetch
-        Node2 N1{}, M1{};  // lane+1's pair and lane-1's B, row r+1
+        P3 = load_row(pin, r + 3, p.ny, p.pitch, cmem);  // prefetch
+        Node2 M1;  // lane-1's B, row r+1 (.y only)
         if (PH >= 1) {
             N1.px = shfl_down2(P1.px, 1); N1.py = shfl_down2(P1.py, 1); N1.pz = shfl_down2(P1.pz, 1);
             N1.vx = shfl_down2(P1.vx, 1); N1.vy = shfl_down2(P1.vy, 1); N1.vz = shfl_down2(P1.vz, 1);
@@ -258,42 +301,22 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
                     kdR2 = __ldg((const float2 *)(kd + 4 * st));
                 }
             }
-        } else if (colint && r >= 0 && r + 2 < p.ny) {
-            // interior strip and rows: every spring exists
-            ksR = ksD = bc(p.ks[0]);
-            kdR = kdD = bc(p.kd[0]);
-            ksDR = ksDL = bc(p.ks[1]);
-            kdDR = kdDL = bc(p.kd[1]);
-            ksR2 = ksD2 = bc(p.ks[2]);
-            kdR2 = kdD2 = bc(p.kd[2]);
         } else {
-            // a spring exists when both ends are grid nodes (A in .x, B in .y)
-            const float2 mR = make_float2(colok(cA) && colok(cA + 1), colok(cA + 1) && colok(cA + 2));
-            const float2 mR2 = make_float2(colok(cA) && colok(cA + 2), colok(cA + 1) && colok(cA + 3));
-            const float2 mD = make_float2(colok(cA), colok(cA + 1));
-            const float2 mDL = make_float2(colok(cA) && colok(cA - 1), colok(cA + 1) && colok(cA));
-            const float rr0 = (r >= 0 && r < p.ny) ? 1.0f : 0.0f;
-            const float rr1 = (r >= 0 && r + 1 < p.ny) ? 1.0f : 0.0f;
-            const float rr2 = (r >= 0 && r + 2 < p.ny) ? 1.0f : 0.0f;
-            const float2 m0 = mul2(mR, bc(rr0)), m2 = mul2(mR2, bc(rr0));
-            const float2 mD1 = mul2(mD, bc(rr1)), mD2m = mul2(mD, bc(rr2));
-            const float2 mDR1 = mul2(mR, bc(rr1)), mDL1 = mul2(mDL, bc(rr1));
-            ksR = mul2(m0, bc(p.ks[0]));
-            kdR = mul2(m0, bc(p.kd[0]));
-            ksD = mul2(mD1, bc(p.ks[0]));
-            kdD = mul2(mD1, bc(p.kd[0]));
-            ksDR = mul2(mDR1, bc(p.ks[1]));
-            kdDR = mul2(mDR1, bc(p.kd[1]));
-            ksDL = mul2(mDL1, bc(p.ks[1]));
-            kdDL = mul2(mDL1, bc(p.kd[1]));
-            ksR2 = mul2(m2, bc(p.ks[2]));
-            kdR2 = mul2(m2, bc(p.kd[2]));
-            ksD2 = mul2(mD2m, bc(p.ks[2]));
-            kdD2 = mul2(mD2m, bc(p.kd[2]));
+            ksR = K.ksR; kdR = K.kdR; ksR2 = K.ksR2; kdR2 = K.kdR2;
+            ksD = K.ksD; kdD = K.kdD; ksD2 = K.ksD2; kdD2 = K.kdD2;
+            ksDR = K.ksDR; kdDR = K.kdDR; ksDL = K.ksDL; kdDL = K.kdDL;
+            if (PH < 2) {
+                // halo rows above the grid own no springs
+                const float2 m0 = bc(r >= 0 ? 1.0f : 0.0f);
+                ksD2 = mul2(ksD2, m0); kdD2 = mul2(kdD2, m0);
+                ksD = mul2(ksD, m0); kdD = mul2(kdD, m0);
+                ksDR = mul2(ksDR, m0); kdDR = mul2(kdDR, m0);
+                ksDL = mul2(ksDL, m0); kdDL = mul2(kdDL, m0);
+            }
         }
 
         // the forward springs of the pair at row r
-        const Vec2 fD2 = spring2(P0, P2, ksD2, kdD2, p.L0[5]);  // (+2,0)
+        Vec2 fD2 = spring2(P0, P2, ksD2, kdD2, p.L0[5]);  // (+2,0)
         Vec2 fD{}, fDR{}, fDL{}, fR{}, fR2{};
         Node2 Q;
         if (PH >= 1) {
@@ -306,6 +329,15 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
             Q.pz = make_float2(M1.pz.y, P1.pz.x); Q.vx = make_float2(M1.vx.y, P1.vx.x);
             Q.vy = make_float2(M1.vy.y, P1.vy.x); Q.vz = make_float2(M1.vz.y, P1.vz.x);
             fDL = spring2(P0, Q, ksDL, kdDL, p.L0[3]);  // (+1,-1)
+        }
+        if (!PER_SPRING && PH >= 1 && r + 2 >= p.ny) {
+            // the grid's last two rows: no (+2,0) springs, and none of
+            // (+1,*) from the last row
+            const float2 m1 = bc(r + 1 < p.ny ? 1.0f : 0.0f);
+            fD2 = {};
+            fD = vscale(fD, m1);
+            fDR = vscale(fDR, m1);
+            fDL = vscale(fDL, m1);
         }
         if (PH == 2) {
             Q.px = make_float2(P0.px.y, N0.px.x); Q.py = make_float2(P0.py.y, N0.py.x);
@@ -338,10 +370,8 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
             const Vec2 bR2 = {shfl_up2(fR2.x, 1), shfl_up2(fR2.y, 1), shfl_up2(fR2.z, 1)};  // (r, c-2)
 
             // F = own forward springs - reactions of the springs that end here
-            Vec2 F = vadd(vadd(vadd(fR, fR2), vadd(fD, fD2)), vadd(fDR, fDL));
-            const Vec2 back = vadd(vadd(vadd(bR, bR2), vadd(fD_1, fD2_2)), vadd(bDR_1, bDL_1));
-            F = vsub(F, back);
-            const bool pinA = pinw & 1u, pinB = (pinw >> 1) & 1u;
+            const Vec2 own = vadd(vadd(vadd(fR, fR2), vadd(fD, fD2)), vadd(fDR, fDL));
+            const Vec2 F = vsub(own, vadd(A1, vadd(bR, bR2)));
 
             float2 ax = fma2(F.x, bc(p.inv_mass), bc(p.g[0]));
             float2 ay = fma2(F.y, bc(p.inv_mass), bc(p.g[1]));
@@ -358,25 +388,27 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
             const float2 dt = bc(p.dt);
             float2 wx = fma2(dt, ax, P0.vx), wy = fma2(dt, ay, P0.vy), wz = fma2(dt, az, P0.vz);
             float2 xx = fma2(dt, wx, P0.px), xy = fma2(dt, wy, P0.py), xz = fma2(dt, wz, P0.pz);
-            // pinned nodes move kinematically: x += dt u, v = u (u = 0: fixed)
-            if (pinA) {
-                xx.x = fmaf(p.dt, p.pin_vel[0], P0.px.x); xy.x = fmaf(p.dt, p.pin_vel[1], P0.py.x);
-                xz.x = fmaf(p.dt, p.pin_vel[2], P0.pz.x);
-                wx.x = p.pin_vel[0]; wy.x = p.pin_vel[1]; wz.x = p.pin_vel[2];
-            }
-            if (pinB) {
-                xx.y = fmaf(p.dt, p.pin_vel[0], P0.px.y); xy.y = fmaf(p.dt, p.pin_vel[1], P0.py.y);
-                xz.y = fmaf(p.dt, p.pin_vel[2], P0.pz.y);
-                wx.y = p.pin_vel[0]; wy.y = p.pin_vel[1]; wz.y = p.pin_vel[2];
+            if (pinw & 3u) {
+                // pinned nodes move kinematically: x += dt u, v = u (u = 0: fixed)
+                if (pinw & 1u) {
+                    xx.x = fmaf(p.dt, p.pin_vel[0], P0.px.x); xy.x = fmaf(p.dt, p.pin_vel[1], P0.py.x);
+                    xz.x = fmaf(p.dt, p.pin_vel[2], P0.pz.x);
+                    wx.x = p.pin_vel[0]; wy.x = p.pin_vel[1]; wz.x = p.pin_vel[2];
+                }
+                if (pinw & 2u) {
+                    xx.y = fmaf(p.dt, p.pin_vel[0], P0.px.y); xy.y = fmaf(p.dt, p.pin_vel[1], P0.py.y);
+                    xz.y = fmaf(p.dt, p.pin_vel[2], P0.pz.y);
+                    wx.y = p.pin_vel[0]; wy.y = p.pin_vel[1]; wz.y = p.pin_vel[2];
+                }
             }
             if (MESH) {
                 // nodes whose path box reaches the box of the non-empty grid
                 // cells are marked for the collision phase after the walk
-                const bool needA = okA && !pinA && fmaxf(P0.px.x, xx.x) >= p.mlo[0] &&
+                const bool needA = okA && !(pinw & 1u) && fmaxf(P0.px.x, xx.x) >= p.mlo[0] &&
                                    fminf(P0.px.x, xx.x) <= p.mhi[0] && fmaxf(P0.py.x, xy.x) >= p.mlo[1] &&
                                    fminf(P0.py.x, xy.x) <= p.mhi[1] && fmaxf(P0.pz.x, xz.x) >= p.mlo[2] &&
                                    fminf(P0.pz.x, xz.x) <= p.mhi[2];
-                const bool needB = okB && !pinB && fmaxf(P0.px.y, xx.y) >= p.mlo[0] &&
+                const bool needB = okB && !(pinw & 2u) && fmaxf(P0.px.y, xx.y) >= p.mlo[0] &&
                                    fminf(P0.px.y, xx.y) <= p.mhi[0] && fmaxf(P0.py.y, xy.y) >= p.mlo[1] &&
                                    fminf(P0.py.y, xy.y) <= p.mhi[1] && fmaxf(P0.pz.y, xz.y) >= p.mlo[2] &&
                                    fminf(P0.pz.y, xz.y) <= p.mhi[2];
@@ -403,22 +435,26 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
                 *(float2 *)(pout.k[5] + o) = wz;
             }
         }
-        // shift the window and the carried forces
-        fD2_2 = fD2_1;
-        fD2_1 = fD2;
-        fD_1 = fD;
-        bDR_1 = nDR;
-        bDL_1 = nDL;
-        P0 = P1;
-        P1 = P2;
-        P2 = P3;
-        N0 = N1;
+        // reactions for the rows below
+        if (PH >= 1) A1 = vadd(D2p, vadd(vadd(fD, nDR), nDL));
+        D2p = fD2;
         r++;
     };
-    row(std::integral_constant<int, 0>());
-    row(std::integral_constant<int, 1>());
-    CLOTH_UNROLL(CLOTH_WALK_UNROLL)
-    while (r < r1) row(std::integral_constant<int, 2>());
+    using PH0 = std::integral_constant<int, 0>;
+    using PH1 = std::integral_constant<int, 1>;
+    using PH2 = std::integral_constant<int, 2>;
+    row(PH0(), Pa, Pb, Pc, Pd, Ne, Nf);
+    row(PH1(), Pb, Pc, Pd, Pa, Nf, Ne);
+    for (;;) {
+        if (r >= r1) break;
+        row(PH2(), Pc, Pd, Pa, Pb, Ne, Nf);
+        if (r >= r1) break;
+        row(PH2(), Pd, Pa, Pb, Pc, Nf, Ne);
+        if (r >= r1) break;
+        row(PH2(), Pa, Pb, Pc, Pd, Ne, Nf);
+        if (r >= r1) break;
+        row(PH2(), Pb, Pc, Pd, Pa, Nf, Ne);
+    }
 
     if (MESH) {
         // append the marked nodes to the collision list, row by row so that
@@ -462,7 +498,7 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
 }
 
 template <bool MESH, bool PER_SPRING>
-__global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) substep_kernel(const StepParams p)
+__global__ void CLOTH_WALK_BOUNDS substep_kernel(const StepParams p)
 {
     __shared__ unsigned long long s_k;
     __shared__ float s_wbase;
@@ -620,7 +656,7 @@ __global__ void __launch_bounds__(256) edge_apply_kernel(const __grid_constant__
 // first), stages that cloth's parameters in its shared-memory slot and walks
 // the strip with the same code as the single-cloth kernel, so every cloth of a
 // batch gets exactly the arithmetic it gets when stepped alone.
-__global__ void __launch_bounds__(32 * WARPS_PER_CTA, CLOTH_WALK_MINB) batch_substep_kernel(const BatchArgs b)
+__global__ void CLOTH_WALK_BOUNDS batch_substep_kernel(const BatchArgs b)
 {
     __shared__ StepParams sp[WARPS_PER_CTA];
     __shared__ unsigned long long s_k;

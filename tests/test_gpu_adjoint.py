@@ -311,3 +311,132 @@ def test_rollout_on_minimal_cloths(cloth_lib, oracle_lib, nx, ny):
     pairs = [(gv0, ov0)] + ([(gks, oks), (gkd, okd)] if S else [])
     for got, ref in pairs:
         assert _l2(got, ref) <= 1e-2
+
+
+def _segment_final(args):
+    """Final FP64 oracle positions and contact signature of a config-4 segment
+    from a given state (worker of a spawned process pool)."""
+    import oracle
+    x0, v0, ks, kd, k0, nsub = args
+    sc = cs.config4()
+    grid = oracle.Grid(sc.mesh_verts, sc.mesh_tris)
+    cl = oracle.Cloth(sc, ks_spring=ks, kd_spring=kd)
+    x, _, sig = oracle.step_signature(cl, x0, v0, k0, nsub, grid)
+    return x, sig
+
+
+@pytest.fixture(scope="module")
+def config4_target(oracle_lib):
+    """The target state of the differentiation workload: the FP64 run with
+    per-spring ks * U(0.8, 1.2) (seed 3) after 256 steps."""
+    sc = cs.config4()
+    grid = oracle_lib.Grid(sc.mesh_verts, sc.mesh_tris)
+    cl = oracle_lib.Cloth(sc, ks_spring=cs.config4_target_ks(sc).astype(np.float64),
+                          kd_spring=sc.kd_spring.astype(np.float64))
+    tgt, _ = oracle_lib.step(cl, sc.init_pos, sc.init_vel, 0, sc.steps * sc.substeps, grid)
+    return tgt
+
+
+@pytest.mark.parametrize("start", [60, 121, 240])
+def test_config4_segment_gradients_match_fd(cloth_lib, oracle_lib, config4_target, start):
+    # The differentiation workload's gradient check with the chaos taken out:
+    # the GPU steps config 4 to `start` (before contact, at contact onset,
+    # resting on the sphere) and its float32 state starts one checkpoint
+    # segment (16 steps) on the GPU and in the FP64 oracle.  Loss = mean
+    # squared distance of the segment's final positions to the workload's
+    # target state.  32 seeded parameters (ks, kd of a spring or a component
+    # of the segment's initial velocity), FP64 central differences at
+    # h = 1e-6 of the oracle from the same float32 start; a parameter is
+    # re-drawn when its +-h or +-h/10 runs change the contact set or the
+    # active hits, or when the two quotients disagree by more than 1e-3.
+    # Bound: rel err <= 1e-3 (floored at 1e-3 of the largest |g_fd|) for the
+    # GPU gradient and for the oracle's adjoint.
+    import multiprocessing as mp
+    P = cloth_lib
+    sc = cs.config4()
+    seg = 16
+    tgt = config4_target
+    with P.Cloth(sc) as cl:
+        cl.step(start)
+        x_s, v_s = cl.read()
+    seg_sc = dataclasses.replace(sc, init_pos=x_s.astype(np.float32), init_vel=v_s.astype(np.float32))
+    k0 = start * sc.substeps
+    nsub = seg * sc.substeps
+    # GPU: one rollout segment from the float32 state (config 4 has no wind,
+    # so a segment does not depend on its start time)
+    gks, gkd, gv0, gpos = _gpu_grads(P, seg_sc, sc.ks_spring, sc.kd_spring, v_s.astype(np.float32), tgt, seg, 16)
+    ks = sc.ks_spring.astype(np.float64)
+    kd = sc.kd_spring.astype(np.float64)
+    x0 = x_s.astype(np.float64)
+    v0 = v_s.astype(np.float64)
+    grid = oracle_lib.Grid(sc.mesh_verts, sc.mesh_tris)
+    cl_o = oracle_lib.Cloth(sc, ks_spring=ks, kd_spring=kd)
+    x_end, _ = oracle_lib.step(cl_o, x0, v0, k0, nsub, grid)
+    dx = float(np.max(np.abs(gpos - x_end)))
+    assert dx < 1e-3, dx  # the 100-step position gate over these 16 steps
+    _, ov0, oks, okd = oracle_lib.adjoint(cl_o, x0, v0, k0, nsub, 2 * (x_end - tgt) / sc.n, np.zeros_like(x_end), grid)
+
+    rng = np.random.default_rng(4 + start)
+    h = 1e-6
+
+    def perturbed(kind, idx, hh):
+        if kind == "v0":
+            i, c = idx
+            vp, vm = v0.copy(), v0.copy()
+            vp[i, c] += hh
+            vm[i, c] -= hh
+            return [(x0, vp, ks, kd, k0, nsub), (x0, vm, ks, kd, k0, nsub)]
+        base = ks if kind == "ks" else kd
+        p, m = base.copy(), base.copy()
+        p[idx] += hh
+        m[idx] -= hh
+        if kind == "ks":
+            return [(x0, v0, p, kd, k0, nsub), (x0, v0, m, kd, k0, nsub)]
+        return [(x0, v0, ks, p, k0, nsub), (x0, v0, ks, m, k0, nsub)]
+
+    jobs, meta = [(x0, v0, ks, kd, k0, nsub)], []
+    for _ in range(64):  # candidates; 32 are kept
+        kind = int(rng.integers(3))
+        if kind == 2:
+            idx = (int(rng.integers(sc.n)), int(rng.integers(3)))
+            meta.append(("v0", idx, gv0[idx], ov0[idx]))
+        else:
+            idx = int(rng.integers(len(ks)))
+            meta.append(("ks" if kind == 0 else "kd", idx, (gks if kind == 0 else gkd)[idx],
+                         (oks if kind == 0 else okd)[idx]))
+        jobs += perturbed(meta[-1][0], idx, h) + perturbed(meta[-1][0], idx, h / 10)
+    with mp.get_context("spawn").Pool(min(16, max(2, mp.cpu_count() or 2))) as pool:
+        res = pool.map(_segment_final, jobs)
+    sig0 = res[0][1]
+
+    def quotient(a, b, hh):
+        (xp, sp), (xm, sm) = a, b
+        dL = float(np.sum((xp - xm) * (xp + xm - 2.0 * tgt)) / len(xp))
+        return dL / (2.0 * hh), sp == sig0 and sm == sig0
+
+    rows = []
+    for j, (kind, idx, g, go) in enumerate(meta):
+        f1, ok1 = quotient(res[1 + 4 * j], res[2 + 4 * j], h)
+        f2, ok2 = quotient(res[3 + 4 * j], res[4 + 4 * j], h / 10)
+        rows.append((kind, idx, g, go, f1, f2, ok1 and ok2))
+    same = [r for r in rows if r[6]]
+    assert len(same) >= 32
+    floor = 1e-3 * max(abs(r[4]) for r in same[:32])
+    got, ora, fds, redrawn = [], [], [], []
+    for kind, idx, g, go, f1, f2, ok in rows:
+        if not ok or abs(f1 - f2) > 1e-3 * max(abs(f1), floor):
+            redrawn.append((kind, idx))
+            continue
+        got.append(g)
+        ora.append(go)
+        fds.append(f1)
+        if len(got) == 32:
+            break
+    assert len(got) == 32
+    fds = np.array(fds)
+    rel_gpu = np.abs(np.array(got) - fds) / np.maximum(np.abs(fds), floor)
+    rel_ora = np.abs(np.array(ora) - fds) / np.maximum(np.abs(fds), floor)
+    print(f"config4 segment from step {start}: max |dx| {dx:.2e} m, re-drawn {redrawn}; max rel err GPU "
+          f"{rel_gpu.max():.2e} oracle adjoint {rel_ora.max():.2e}")
+    assert rel_ora.max() <= 1e-3, rel_ora
+    assert rel_gpu.max() <= 1e-3, rel_gpu
