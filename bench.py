@@ -12,9 +12,14 @@ broad phase, MT narrow phase, response) over all nodes.
 
 Prints one JSON line.  `value` is whole-job node-steps/s with the state
 resident in HBM (per-step CUDA events on the library's stream, L2 flushed by
-a 256 MiB write before every timed step); `e2e` is the same metric through
-the C ABI with pinned host buffers copied in and out every step.  Under
-torchrun every rank steps its own replica of the cloth (no exchange).
+a 256 MiB write before every timed step).  The timed window starts at step
+600 of the workload, with the cloth resting on the mesh, so every timed step
+runs the narrow phase and the response; `collision` gives the listed nodes,
+candidate tests and hit nodes per substep of the window.  `e2e` is the same
+metric through the C ABI with pinned host buffers copied in and out every
+step (the input is the window's starting state).  `configs` times the other
+synthetic workloads over their configured steps next to the FP64 oracle.
+Under torchrun every rank steps its own replica of the cloth (no exchange).
 `--impl reference` times the FP64 CPU oracle on the host on a bounded row
 band of the same workload.
 """
@@ -35,6 +40,9 @@ sys.path.insert(0, ROOT)
 METRIC = "node-steps/s at 640K nodes + 100K-tri collision; HBM roofline %; adjoint vs fwd"
 UNIT = "node-steps/s"
 BYTES_PER_NODE_SUBSTEP = 48  # read p, v (24 B) + write p, v (24 B), float32 SoA
+START_STEP = 600    # the timed window starts here (the cloth rests on the mesh)
+HEAT_STEPS = 300    # untimed steps just before it, under the clock sampler
+LAUNCHES_PER_SUBSTEP = 2  # walk + collision kernel
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "substep_kernel_800x800_l6.txt")
 STEP_SRC = os.path.join(ROOT, "paper_2507_11794_gb300", "csrc", "cloth_step.cu")
 
@@ -55,11 +63,13 @@ def parse():
 
 
 def workload_config(sc):
-    return {
+    return {"start_step": START_STEP,
         "workload": "800x800 grid cloth (640,000 nodes, 3,832,002 springs), top row pinned, gravity + 2 N/kg "
                     "sinusoidal wind, vs 81,920-triangle displaced icosphere r=0.25 m; dt=1/1200 s, 4 substeps",
         "nodes": sc.n, "springs": 3832002, "triangles": int(sc.ntris), "substeps_per_step": sc.substeps,
         "dt": sc.dt, "l2": "flushed (256 MiB write) before every timed step",
+        "timed_window": f"steps {START_STEP}.. of the workload (contact phase), after {START_STEP} untimed steps "
+                        "from its initial state",
         "parallelism": "replicas",
     }
 
@@ -146,13 +156,15 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, window=None):
         """Median SM clock, max clock and active slowdown reasons over the
-        samples taken inside the marked timed region (plus the sample either
-        side of it, which brackets a region shorter than the sampling period)."""
+        samples taken inside a window (default: the marked timed region),
+        plus the sample either side of it, which brackets a window shorter
+        than the sampling period."""
         rows = [r for r in self.rows if len(r) >= 10]
-        if self.window is not None and rows:
-            t0, t1 = self.window
+        window = window or self.window
+        if window is not None and rows:
+            t0, t1 = window
             inside = [i for i, r in enumerate(rows) if t0 <= r[-1] <= t1]
             before = [i for i, r in enumerate(rows) if r[-1] < t0][-1:]
             after = [i for i, r in enumerate(rows) if r[-1] > t1][:1]
@@ -210,6 +222,54 @@ def max_over_ranks(pg, x: float) -> float:
     return float(t.item())
 
 
+def host_cpu():
+    """CPU model and logical core count of this host."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":", 1)[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"cpu_model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
+def oracle_rate(sc, steps: int, rows: int | None = None):
+    """Node-steps/s of the FP64 oracle (1 thread) on the first `rows` rows of
+    a scene (all rows by default) for `steps` steps from its initial state,
+    with the scene's own mesh.  Returns (rate, seconds, nodes)."""
+    import dataclasses
+
+    import numpy as np
+
+    import oracle
+    rows = sc.ny if rows is None else min(rows, sc.ny)
+    nx = sc.nx
+    sub = dataclasses.replace(sc, ny=rows, init_pos=sc.init_pos[:rows * nx], init_vel=sc.init_vel[:rows * nx],
+                              pinned=sc.pinned[:rows * nx])
+    cl = oracle.Cloth(sub)
+    grid = oracle.Grid(sub.mesh_verts, sub.mesh_tris) if sub.mesh_tris is not None else None
+    x, v = sub.init_pos, sub.init_vel
+    t0 = time.perf_counter()
+    x, v = oracle.step(cl, x, v, 0, steps * sub.substeps, grid)
+    dt = time.perf_counter() - t0
+    assert np.all(np.isfinite(x))
+    return rows * nx * steps / dt, dt, rows * nx
+
+
 def cpu_oracle_sample(sc, rows: int, steps: int):
     """Time the FP64 oracle on the first `rows` rows of the cloth for `steps`
     steps (1 thread).  Returns (node-steps/s, seconds, nodes)."""
@@ -230,6 +290,78 @@ def cpu_oracle_sample(sc, rows: int, steps: int):
     dt = time.perf_counter() - t0
     assert np.all(np.isfinite(x))
     return rows * nx * steps / dt, dt, rows * nx
+
+
+def cpu_oracle_band(sc, x, v, row0: int, rows: int, steps: int, k0: int):
+    """Time the FP64 oracle (1 thread) on rows [row0, row0 + rows) of the
+    cloth, started from the given float32 state at global substep k0, with
+    the full mesh, for `steps` steps.  Returns (node-steps/s, seconds, nodes)."""
+    import dataclasses
+
+    import numpy as np
+
+    import oracle
+    nx = sc.nx
+    sl = slice(row0 * nx, (row0 + rows) * nx)
+    sub = dataclasses.replace(sc, ny=rows, init_pos=np.ascontiguousarray(x[sl]), init_vel=np.ascontiguousarray(v[sl]),
+                              pinned=np.ascontiguousarray(sc.pinned[sl]),
+                              origin=tuple(float(sc.origin[a] + row0 * sc.dv[a]) for a in range(3)))
+    cl = oracle.Cloth(sub)
+    grid = oracle.Grid(sub.mesh_verts, sub.mesh_tris)
+    t0 = time.perf_counter()
+    xo, _ = oracle.step(cl, sub.init_pos, sub.init_vel, k0, steps * sub.substeps, grid)
+    dt = time.perf_counter() - t0
+    assert np.all(np.isfinite(xo))
+    return rows * nx * steps / dt, dt, rows * nx
+
+
+def run_config_legs(stream, flush, peak):
+    """The other synthetic workloads, each over its configured steps from its
+    initial state (per-step CUDA events, L2 flushed before every step):
+    node-steps/s, the whole-step HBM fraction (48 B per node-substep over the
+    step time) and the FP64 oracle's rate on a bounded sample (1 thread)."""
+    import numpy as np
+    import torch
+
+    import cloth_scenes as cs
+    import paper_2507_11794_gb300 as P
+    legs = {}
+    specs = [("config1_32x32_L2", cs.config1(), None, 200),
+             ("config2_256x256_L6", cs.config2(), None, 30),
+             ("config3i_800x800_none", cs.config3("none"), 400, 30),
+             ("config3ii_800x800_L5", cs.config3("l5"), 400, 30)]
+    for name, sc, rows, osteps in specs:
+        cl = P.Cloth(sc, stream=int(stream.cuda_stream))
+        cl.step(2)
+        cl.set_state(sc.init_pos, sc.init_vel)
+        cl.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(sc.steps)]
+        for i in range(sc.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            cl.step(1)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / sc.steps
+        listed, tested, hits = cl.collision_stats()
+        pos, _ = cl.read()
+        assert np.all(np.isfinite(pos))
+        cl.close()
+        val = sc.n / (ms / 1e3)
+        achieved = BYTES_PER_NODE_SUBSTEP * sc.n * sc.substeps / (ms * 1e-3) / 1e9
+        orate, odt, onodes = oracle_rate(sc, osteps, rows)
+        nsub = sc.steps * sc.substeps
+        legs[name] = {"nodes": sc.n, "triangles": sc.ntris, "steps": sc.steps, "substeps_per_step": sc.substeps,
+                      "ms_per_step": ms, "node_steps_per_s": val,
+                      "node_substeps_per_s": val * sc.substeps,
+                      "hbm_frac_whole_step": achieved / peak, "achieved_gbs_whole_step": achieved,
+                      "mean_listed_per_substep": listed / (nsub + 2 * sc.substeps),
+                      "mean_tested_per_substep": tested / (nsub + 2 * sc.substeps),
+                      "oracle_node_steps_per_s": orate,
+                      "oracle_sample": f"{'all' if rows is None else f'first {rows}'} rows ({onodes} nodes), "
+                                       f"{osteps} steps from the initial state, FP64, 1 thread, {odt:.1f} s",
+                      "gpu_over_oracle": val / orate}
+    return legs
 
 
 def run_reference(args):
@@ -483,14 +615,25 @@ def run_ours(args):
         flush.fill_(1.0)
         cl.step(1)
     cl.sync()
-    cl.set_state(sc.init_pos, sc.init_vel)  # timed run starts from the workload's initial state
+    # the timed window starts in the contact phase: from the workload's
+    # initial state, START_STEP steps run untimed, the last HEAT of them with
+    # the same L2 flushes as the timed steps (the clock sampler covers them)
+    cl.set_state(sc.init_pos, sc.init_vel)
+    heat = min(HEAT_STEPS, START_STEP)
+    cl.step(START_STEP - heat)
     cl.sync()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    barrier(pg)
-    torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clocks:
+        h0 = time.perf_counter()
+        for i in range(heat):
+            flush.fill_(float(i))
+            cl.step(1)
+        stats0 = cl.collision_stats()  # synchronises
+        x_start, v_start = cl.read()
+        barrier(pg)
+        torch.cuda.synchronize()
         wall0 = time.perf_counter()
         for i in range(args.steps):
             flush.fill_(float(i))
@@ -501,36 +644,47 @@ def run_ours(args):
         wall = time.perf_counter() - wall0
         clocks.mark(wall0, wall0 + wall)
     barrier(pg)
-    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    stats1 = cl.collision_stats()
+    nsub_timed = args.steps * SUB
+    coll = {"listed_per_substep": (stats1[0] - stats0[0]) / nsub_timed,
+            "tested_per_substep": (stats1[1] - stats0[1]) / nsub_timed,
+            "hit_nodes_per_substep": (stats1[2] - stats0[2]) / nsub_timed}
+    dev_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
     pos, vel = cl.read()
     assert np.all(np.isfinite(pos)) and np.all(np.isfinite(vel))
     t = max_over_ranks(pg, dev_ms / 1e3)
     value = ws * N * args.steps / t
-    launches = 2 * SUB * args.steps  # walk + collision kernel per substep
+    launches = LAUNCHES_PER_SUBSTEP * SUB * args.steps
 
-    # per-kernel durations: the same steps (L2 flushed before each), every
-    # kernel launch bracketed by CUDA events on the library's stream
+    # kernel split: the same steps (L2 flushed before each), every kernel
+    # launch bracketed by CUDA events on the library's stream; the events
+    # stop each launch from overlapping the previous one's tail, so these
+    # durations only give the walk's share of the substep, which is applied
+    # to the timed substep
     prof_steps = min(args.steps, 200)
-    walk_us = coll_us = 0.0
+    walk_ev = coll_ev = 0.0
     for i in range(prof_steps):
         flush.fill_(float(i))
         w, c = cl.profile_substeps(SUB)
-        walk_us += w / prof_steps
-        coll_us += c / prof_steps
+        walk_ev += w / prof_steps
+        coll_ev += c / prof_steps
 
-    # end to end through the C ABI: pinned host state in, step, state out
+    # end to end through the C ABI: pinned host state in (the contact-phase
+    # state the timed window started from), step, state out
     ke = args.e2e_steps or min(args.steps, 1000)
     hp = torch.empty((N, 3), dtype=torch.float32, pin_memory=True).numpy()
     hv = torch.empty((N, 3), dtype=torch.float32, pin_memory=True).numpy()
-    hp[:] = sc.init_pos
-    hv[:] = sc.init_vel
+    op = torch.empty((N, 3), dtype=torch.float32, pin_memory=True).numpy()
+    ov = torch.empty((N, 3), dtype=torch.float32, pin_memory=True).numpy()
+    hp[:] = x_start
+    hv[:] = v_start
     barrier(pg)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     for _ in range(ke):
         cl.set_state(hp, hv)
         cl.step(1)
-        cl.read(out_pos=hp, out_vel=hv)
+        cl.read(out_pos=op, out_vel=ov)
     e2e_t = max_over_ranks(pg, time.perf_counter() - e0)
     e2e_val = ws * N * ke / e2e_t
 
@@ -562,21 +716,30 @@ def run_ours(args):
     peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
     normals["frac"] = normals["achieved_gbs"] / peak
     peak_src = "measured" if peaks and "hbm_gbs" in peaks else "fallback"
+    us_sub = 1e3 * (t / args.steps) * 1e3 / SUB  # timed substep, us
+    share = walk_ev / (walk_ev + coll_ev) if walk_ev + coll_ev > 0 else 1.0
+    walk_us = us_sub * share
     achieved = BYTES_PER_NODE_SUBSTEP * N / (walk_us * 1e-6) / 1e9
+    step_achieved = BYTES_PER_NODE_SUBSTEP * N / (us_sub * 1e-6) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profile_traffic(), "peak_source": peak_src,
                 "kernel": "substep_kernel<MESH=true> (walk: springs + integration)",
                 "algorithmic_bytes_per_launch": BYTES_PER_NODE_SUBSTEP * N,
-                "avg_launch_us": walk_us, "collide_kernel_avg_launch_us": coll_us,
-                "timing": f"CUDA events around each launch, {prof_steps} steps x {SUB} substeps after the timed "
-                          f"region, L2 flushed before each step"}
+                "avg_launch_us": walk_us,
+                "timing": "timed substep (ms_per_step / substeps) x the walk's share of the substep's kernel time; "
+                          "the share is from event-bracketed launches over the next steps",
+                "walk_share": share, "event_bracketed_walk_us": walk_ev, "event_bracketed_collide_us": coll_ev,
+                "whole_substep": {"us": us_sub, "achieved": step_achieved, "frac": step_achieved / peak}}
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        rows, csteps = 400, 30
-        val, dt, nodes = cpu_oracle_sample(sc, rows, csteps)
-        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {rows} rows ({nodes} nodes) of the same cloth with the full mesh, {csteps} steps "
-                         f"x 4 substeps from the initial state ({dt:.1f} s, FP64, 1 thread)"}
+        row0, rows, csteps = 280, 400, 10
+        val, dt, nodes = cpu_oracle_band(sc, x_start, v_start, row0, rows, csteps, START_STEP * SUB)
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", **host_cpu(),
+               "sample": f"rows {row0}-{row0 + rows - 1} ({nodes} nodes) of the cloth's float32 state at step "
+                         f"{START_STEP} (the timed window's start, in contact with the mesh), {csteps} steps x 4 "
+                         f"substeps with the full mesh ({dt:.1f} s, FP64, 1 thread)"}
+    legs = None if args.no_batch else run_config_legs(stream, flush, peak)
+    heat_clocks = clocks.summary((h0, wall0 + wall))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -584,7 +747,9 @@ def run_ours(args):
            "roofline": roofline, "cpu_baseline": cpu,
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 12 * N,
                    "d2h_bytes_per_step": 2 * 12 * N, "steps": ke},
-           "gpu_launches": launches, "clocks": clocks.summary(), "batch": batch, "adjoint": adjoint, "atomic_springs_ab": atomic_ab, "edge_narrow_phase_ab": edge_ab, "pulling_scene": pulling,
+           "gpu_launches": launches, "clocks": {**clocks.summary(), "heat_and_timed": heat_clocks},
+           "collision": coll, "batch": batch, "adjoint": adjoint, "atomic_springs_ab": atomic_ab,
+           "edge_narrow_phase_ab": edge_ab, "pulling_scene": pulling, "configs": legs,
            "normals": normals,
            "wall_s_timed_loop": wall}
     print(json.dumps(out), flush=True)

@@ -117,6 +117,10 @@ class Cloth:
     def info(self):
         return capi.cloth_get_info(self.h)
 
+    def collision_stats(self):
+        """(listed, tested, hits) summed over all substeps since create."""
+        return capi.cloth_get_collision_stats(self.h)
+
     def normals(self, out=None):
         """Per-vertex normals of the current state as a (N, 3) float32 CUDA
         tensor (``out`` if given)."""

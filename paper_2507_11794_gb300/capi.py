@@ -34,7 +34,7 @@ _NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5
 
 # Every symbol include/cloth.h declares (checked by the CPU test-suite).
 EXPORTS = ("cloth_create", "cloth_set_mesh", "cloth_step", "cloth_read", "cloth_destroy",
-           "cloth_set_state", "cloth_sync", "cloth_last_error", "cloth_get_info", "cloth_get_grid",
+           "cloth_set_state", "cloth_sync", "cloth_get_collision_stats", "cloth_last_error", "cloth_get_info", "cloth_get_grid",
            "cloth_query_candidates", "cloth_grid_build_static", "cloth_profile_substeps",
            "cloth_compute_normals",
            "cloth_batch_create", "cloth_batch_set_mesh", "cloth_batch_step", "cloth_batch_read",
@@ -118,6 +118,8 @@ def lib():
         L.cloth_destroy.restype = None
         L.cloth_set_state.argtypes = [H, fp, fp]
         L.cloth_sync.argtypes = [H]
+        L.cloth_get_collision_stats.argtypes = [H, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                                C.POINTER(C.c_int64)]
         L.cloth_last_error.argtypes = []
         L.cloth_last_error.restype = C.c_char_p
         L.cloth_get_info.argtypes = [H, C.POINTER(ClothInfo)]
@@ -205,6 +207,13 @@ def cloth_set_state(h: int, pos=None, vel=None):
 
 def cloth_sync(h: int):
     check(lib().cloth_sync(h))
+
+
+def cloth_get_collision_stats(h: int):
+    """(listed, tested, hits): running collision totals since create."""
+    v = [C.c_int64(0) for _ in range(3)]
+    check(lib().cloth_get_collision_stats(h, *(C.byref(x) for x in v)))
+    return tuple(int(x.value) for x in v)
 
 
 def cloth_destroy(h: int):

@@ -257,6 +257,9 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
     // kernels index a plane with 32-bit offsets r * pitch + c
     if ((long long)((d.nx + 3) / 4 * 4) * d.ny >= (1ll << 31))
         return fail(CLOTH_ERR_INVALID_ARG, "plane of %d x %d nodes too large", d.nx, d.ny);
+    // and the six planes of a state buffer with 32-bit offsets j * stride + o
+    if (6 * (((long long)((d.nx + 3) / 4 * 4) * d.ny + 63) / 64 * 64) >= (1ll << 32))
+        return fail(CLOTH_ERR_INVALID_ARG, "plane of %d x %d nodes too large for 32-bit state offsets", d.nx, d.ny);
     if (d.substeps < 1) return fail(CLOTH_ERR_INVALID_ARG, "substeps must be >= 1");
     if (!(d.dt > 0.0f) || !isfinite(d.dt)) return fail(CLOTH_ERR_INVALID_ARG, "dt must be finite and > 0");
     if (!(d.total_mass > 0.0f) || !isfinite(d.total_mass))
@@ -581,6 +584,21 @@ int cloth_sync(ClothHandle *h)
     rc = read_flags(h, &flags);
     if (rc) return rc;
     return flags_status(flags);
+}
+
+int cloth_get_collision_stats(ClothHandle *h, int64_t *listed, int64_t *tested, int64_t *hits)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    DeviceScope ds(h->device);
+    unsigned long long v[3] = {0ull, 0ull, 0ull};
+    CTRY(h, cudaMemcpyAsync(v, &h->ctrl->stat_listed, sizeof(v), cudaMemcpyDeviceToHost, h->stream),
+         "read collision statistics");
+    CTRY(h, cudaStreamSynchronize(h->stream), "synchronize");
+    if (listed) *listed = (int64_t)v[0];
+    if (tested) *tested = (int64_t)v[1];
+    if (hits) *hits = (int64_t)v[2];
+    return CLOTH_OK;
 }
 
 void cloth_destroy(ClothHandle *h)

@@ -158,11 +158,14 @@ struct CollLane {
     int2 cell[COLL_MAXC];       // per cell of the box: first entry, end of the lane's running count
 };
 
-struct CollShared {
-    CollLane lane[COLL_WARPS][32];
-    int base[COLL_WARPS][32];    // first candidate index of each lane (warp exclusive scan)
-    float val[COLL_WARPS][32];   // one round's results: max(t - delta, 0) on a hit, else -1
+// Per-warp scratch of the cooperative pass, for a CTA of W warps.
+template <int W>
+struct CollSharedT {
+    CollLane lane[W][32];
+    int base[W][32];    // first candidate index of each lane (warp exclusive scan)
+    float val[W][32];   // one round's results: max(t - delta, 0) on a hit, else -1
 };
+using CollShared = CollSharedT<COLL_WARPS>;
 // The recording variant adds each candidate's terms of g1 and g2.
 struct CollSharedRec : CollShared {
     float g[COLL_WARPS][6][32];
@@ -193,15 +196,17 @@ __device__ __forceinline__ void coll_record(const StepParams &p, long long o, fl
 // Src supplies per list entry i: entry(i, cloth, offset) and params(cloth).
 // REC (with CollSharedRec): also sums, over the active hits in the same
 // order, g1 and g2 as collide_t<true> does and records them (coll_record).
-template <bool REC = false, class Src, class Sh>
-__device__ __forceinline__ void collide_list(const Src &src, Sh &sh, unsigned long long k, unsigned n, float &fsum)
+// One round of the cooperative pass: every lane of the warp brings one entry
+// (valid: whether it has one; i: its index for src.entry).  ntest (lane 0)
+// accumulates the candidate triangles the warp tested, nhit (every lane) the
+// nodes that hit.
+template <bool REC, class Src, class Sh>
+__device__ __forceinline__ void collide_batch(const Src &src, Sh &sh, unsigned long long k, bool valid,
+                                              unsigned long long i, float &fsum, unsigned &ntest, unsigned &nhit)
 {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const unsigned long long nw = (unsigned long long)gridDim.x * COLL_WARPS;
-    const unsigned long long w = (unsigned long long)blockIdx.x * COLL_WARPS + wib;
     CollLane &me = sh.lane[wib][lane];
-    for (unsigned long long b0 = 0; b0 < n; b0 += 32ull * nw) {
-        const unsigned long long i = b0 + (unsigned long long)lane * nw + w;
+    {
         int cnt = 0, cloth = 0;
         bool serial = false;
         long long o = 0;
@@ -209,7 +214,7 @@ __device__ __forceinline__ void collide_list(const Src &src, Sh &sh, unsigned lo
         CollPath q;
         float *out = nullptr;
         long long st = 0;
-        if (i < n) {
+        if (valid) {
             src.entry(i, cloth, o);
             const StepParams &p = src.params(cloth);
             st = p.stride;
@@ -245,6 +250,7 @@ __device__ __forceinline__ void collide_list(const Src &src, Sh &sh, unsigned lo
             if (lane >= d) incl += t;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (lane == 0) ntest += (unsigned)total;
         const int excl = incl - cnt;
         sh.base[wib][lane] = excl;
         __syncwarp();
@@ -311,7 +317,7 @@ __device__ __forceinline__ void collide_list(const Src &src, Sh &sh, unsigned lo
             }
             __syncwarp();
         }
-        if (i >= n) continue;
+        if (!valid) return;
         const StepParams &p = src.params(cloth);
         float ox, oy, oz;
         bool hit;
@@ -341,7 +347,43 @@ __device__ __forceinline__ void collide_list(const Src &src, Sh &sh, unsigned lo
             out[4 * st + o] *= p.restitution;
             out[5 * st + o] *= p.restitution;
             fsum += ox + oy + oz;
+            nhit++;
         }
+    }
+}
+
+// The cooperative pass over a list of n entries: entry i goes to warp
+// i mod #warps (see above), 32 entries per warp and round.
+template <bool REC = false, class Src, class Sh>
+__device__ __forceinline__ void collide_list(const Src &src, Sh &sh, unsigned long long k, unsigned n, float &fsum,
+                                             unsigned &ntest, unsigned &nhit)
+{
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned long long nw = (unsigned long long)gridDim.x * COLL_WARPS;
+    const unsigned long long w = (unsigned long long)blockIdx.x * COLL_WARPS + wib;
+    for (unsigned long long b0 = 0; b0 < n; b0 += 32ull * nw) {
+        const unsigned long long i = b0 + (unsigned long long)lane * nw + w;
+        collide_batch<REC>(src, sh, k, i < n, i, fsum, ntest, nhit);
+    }
+}
+
+// Adds a collision pass's counts to the cloth's running statistics: every
+// warp's tested candidates and hit nodes are summed per CTA in shared memory
+// (s2, zeroed by the caller before a __syncthreads), then one thread adds the
+// CTA's totals; CTA 0 also adds the list length n.  The adds return nothing,
+// so no thread waits on them.
+__device__ __forceinline__ void coll_stats_add(DevCtrl *ctrl, unsigned *s2, unsigned n, unsigned ntest, unsigned nhit)
+{
+    const unsigned h = __reduce_add_sync(0xffffffffu, nhit);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s2[0], ntest);
+        atomicAdd(&s2[1], h);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s2[0]) atomicAdd(&ctrl->stat_tested, (unsigned long long)s2[0]);
+        if (s2[1]) atomicAdd(&ctrl->stat_hits, (unsigned long long)s2[1]);
+        if (blockIdx.x == 0) atomicAdd(&ctrl->stat_listed, (unsigned long long)n);
     }
 }
 

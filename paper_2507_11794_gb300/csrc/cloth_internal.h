@@ -13,6 +13,9 @@ struct DevCtrl {
     unsigned int flags;       // CTRL_FLAG_* (sticky until set_state)
     unsigned int coll_count;  // marked nodes of the running substep
     unsigned int pad;
+    // running collision statistics since create: listed nodes, candidate
+    // triangles tested, nodes that hit (summed over substeps)
+    unsigned long long stat_listed, stat_tested, stat_hits;
 };
 
 enum : unsigned int { CTRL_FLAG_NONFINITE = 1u, CTRL_FLAG_TIMEOUT = 2u };

@@ -110,30 +110,23 @@ __device__ __forceinline__ float2 shfl_up2(float2 v, int d)
 {
     return make_float2(__shfl_up_sync(FULL, v.x, d), __shfl_up_sync(FULL, v.y, d));
 }
-// Six plane pointers of one state buffer.
-struct Planes {
-    float *k[6];
-};
-__device__ __forceinline__ Planes planes(float *base, long long st)
-{
-    return {{base, base + st, base + 2 * st, base + 3 * st, base + 4 * st, base + 5 * st}};
-}
-
 // Row r of the lane's two columns.  The row and the column pair are clamped
 // into the grid's memory, so every load is in bounds; the values of a row
 // outside [0, ny) or a pair outside the pitch are finite stand-ins that only
-// enter springs whose constants are zero (no spring there).
-__device__ __forceinline__ Node2 load_row(const Planes &in, int r, int ny, int pitch, int cmem)
+// enter springs whose constants are zero (no spring there).  Plane j of the
+// buffer starts at in + j * st (32-bit offsets: creation keeps 6 st below
+// 2^32).
+__device__ __forceinline__ Node2 load_row(const float *in, unsigned st, int r, int ny, int pitch, int cmem)
 {
     const int rr = min(max(r, 0), ny - 1);
     const unsigned o = (unsigned)rr * (unsigned)pitch + (unsigned)cmem;
     Node2 n;
-    n.px = __ldg((const float2 *)(in.k[0] + o));
-    n.py = __ldg((const float2 *)(in.k[1] + o));
-    n.pz = __ldg((const float2 *)(in.k[2] + o));
-    n.vx = __ldg((const float2 *)(in.k[3] + o));
-    n.vy = __ldg((const float2 *)(in.k[4] + o));
-    n.vz = __ldg((const float2 *)(in.k[5] + o));
+    n.px = __ldg((const float2 *)(in + o));
+    n.py = __ldg((const float2 *)(in + (o + st)));
+    n.pz = __ldg((const float2 *)(in + (o + 2u * st)));
+    n.vx = __ldg((const float2 *)(in + (o + 3u * st)));
+    n.vy = __ldg((const float2 *)(in + (o + 4u * st)));
+    n.vz = __ldg((const float2 *)(in + (o + 5u * st)));
     return n;
 }
 
@@ -156,11 +149,44 @@ __device__ __forceinline__ Vec2 spring2(const Node2 &P, const Node2 &Q, float2 k
 
 __device__ __forceinline__ Vec2 vscale(Vec2 a, float2 s) { return {mul2(a.x, s), mul2(a.y, s), mul2(a.z, s)}; }
 
-// Per-lane spring constants of a strip: the type's ks, kd where the spring
-// exists for the lane's columns (both ends inside the grid), else zero.
-struct LaneK {
-    float2 ksR, kdR, ksR2, kdR2, ksD, kdD, ksD2, kdD2, ksDR, kdDR, ksDL, kdDL;
+
+// Inputs of a strip that do not change from substep to substep (the wind
+// tables and the pin bits): the lane's column wind terms and the first output
+// row's entries.  The single-cloth kernel loads them before it waits for the
+// previous substep, so their latency hides behind that wait.
+struct WalkStatics {
+    float2 sinB, cosB;  // (sin, cos) of the column phase of the lane's two columns
+    float2 trN;         // (sin, cos) of row r0's phase
+    unsigned pinN;      // the pin word holding row r0's bit of the lane's column A
 };
+
+__device__ __forceinline__ WalkStatics walk_statics(const StepParams &p, int sx, int sy, int lane)
+{
+    WalkStatics w;
+    const int cA = sx * STRIP_COLS - 2 + 2 * lane;
+    const int r0 = sy * p.rows_per_warp;
+    w.sinB = w.cosB = make_float2(0.0f, 0.0f);
+    w.trN = make_float2(0.0f, 1.0f);
+    w.pinN = 0u;
+    if (p.has_wind) {
+        if (cA >= 0 && cA < p.nx) {
+            const float2 t = __ldg(p.wind_cols + cA);
+            w.sinB.x = t.x;
+            w.cosB.x = t.y;
+        }
+        if (cA + 1 >= 0 && cA + 1 < p.nx) {
+            const float2 t = __ldg(p.wind_cols + cA + 1);
+            w.sinB.y = t.x;
+            w.cosB.y = t.y;
+        }
+        if (r0 < p.ny) w.trN = __ldg(p.wind_rows + r0);
+    }
+    if (p.pin_bits && cA >= 0 && cA < p.pitch && r0 < p.ny) {
+        const unsigned o = (unsigned)r0 * (unsigned)p.pitch + (unsigned)cA;
+        w.pinN = __ldg(p.pin_bits + (o >> 5));
+    }
+    return w;
+}
 
 // One warp's strip: columns [60 sx - 2, 60 sx + 62) walked down rows
 // [r0 - 2, r0 + rows_per_warp) with a register window of rows r .. r+2 (row
@@ -179,10 +205,10 @@ struct LaneK {
 template <bool MESH, bool PER_SPRING>
 __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__restrict__ in, float *__restrict__ out,
                                            float wbase, int sx, int sy, int lane, int cloth,
-                                           float2 &fsum)
+                                           float2 &fsum, const WalkStatics &ws)
 {
     const long long st = p.stride;
-    const Planes pin = planes(const_cast<float *>(in), st), pout = planes(out, st);
+    const unsigned st32 = (unsigned)st;
     const int cA = sx * STRIP_COLS - 2 + 2 * lane;  // column of node A (even)
     const int r0 = sy * p.rows_per_warp;
     const int r1 = min(r0 + p.rows_per_warp, p.ny);  // output rows [r0, r1)
@@ -192,65 +218,49 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
     auto colok = [&](int c) { return c >= 0 && c < p.nx; };
     const bool okA = out_lane && colok(cA), okB = out_lane && colok(cA + 1);
 
-    LaneK K;
+    // which of the lane's springs exist column-wise (both ends inside the
+    // grid; A in the even bit, B in the odd bit of each pair): right, right2,
+    // down (and down2), down-left; down-right exists where right does
+    unsigned cm = 0u;
     if (!PER_SPRING) {
-        // a spring exists when both ends are grid nodes (A in .x, B in .y)
-        const float2 mR = make_float2(colok(cA) && colok(cA + 1), colok(cA + 1) && colok(cA + 2));
-        const float2 mR2 = make_float2(colok(cA) && colok(cA + 2), colok(cA + 1) && colok(cA + 3));
-        const float2 mD = make_float2(colok(cA), colok(cA + 1));
-        const float2 mDL = make_float2(colok(cA) && colok(cA - 1), colok(cA + 1) && colok(cA));
-        K.ksR = mul2(mR, bc(p.ks[0]));
-        K.kdR = mul2(mR, bc(p.kd[0]));
-        K.ksD = mul2(mD, bc(p.ks[0]));
-        K.kdD = mul2(mD, bc(p.kd[0]));
-        K.ksDR = mul2(mR, bc(p.ks[1]));
-        K.kdDR = mul2(mR, bc(p.kd[1]));
-        K.ksDL = mul2(mDL, bc(p.ks[1]));
-        K.kdDL = mul2(mDL, bc(p.kd[1]));
-        K.ksR2 = mul2(mR2, bc(p.ks[2]));
-        K.kdR2 = mul2(mR2, bc(p.kd[2]));
-        K.ksD2 = mul2(mD, bc(p.ks[2]));
-        K.kdD2 = mul2(mD, bc(p.kd[2]));
+        cm = (colok(cA) && colok(cA + 1)) | (colok(cA + 1) && colok(cA + 2)) << 1 |
+             (colok(cA) && colok(cA + 2)) << 2 | (colok(cA + 1) && colok(cA + 3)) << 3 |
+             colok(cA) << 4 | colok(cA + 1) << 5 | (colok(cA) && colok(cA - 1)) << 6 |
+             (colok(cA + 1) && colok(cA)) << 7;
     }
+    // strips whose lanes all have every spring take the constants unmasked
+    const bool edge_strip = !PER_SPRING && __any_sync(FULL, cm != 0xffu);
+    auto cmask = [&](int b) {
+        return make_float2((cm >> b) & 1u ? 1.0f : 0.0f, (cm >> (b + 1)) & 1u ? 1.0f : 0.0f);
+    };
 
     // wind: sin(base + alpha_r + beta_c) from per-row and per-column tables of
     // (sin, cos) and the addition formula; depends only on (row, col, time)
-    float2 sinB = bc(0.0f), cosB = bc(0.0f);
+    const float2 sinB = ws.sinB, cosB = ws.cosB;
     float sinW = 0.0f, cosW = 1.0f;
-    if (p.has_wind) {
-        if (cA >= 0 && cA < p.nx) {
-            const float2 t = __ldg(p.wind_cols + cA);
-            sinB.x = t.x;
-            cosB.x = t.y;
-        }
-        if (cA + 1 >= 0 && cA + 1 < p.nx) {
-            const float2 t = __ldg(p.wind_cols + cA + 1);
-            sinB.y = t.x;
-            cosB.y = t.y;
-        }
-        sincosf(wbase, &sinW, &cosW);
-    }
-    // per-row inputs, fetched one row ahead: the row's wind table entry and pin bits
-    auto row_inputs = [&](int r, float2 &tr, unsigned &pinw) {
+    if (p.has_wind) sincosf(wbase, &sinW, &cosW);
+    // per-row inputs, fetched one row ahead: the row's wind table entry and
+    // the word holding its pin bits (shifted where it is used, so that no
+    // instruction waits for the load until the next row)
+    auto row_inputs = [&](int r, float2 &tr, unsigned &pinword) {
         tr = make_float2(0.0f, 1.0f);
-        pinw = 0u;
+        pinword = 0u;
         if (r < r1) {
             if (p.has_wind) tr = __ldg(p.wind_rows + r);
             if (p.pin_bits && colmem) {
                 const unsigned o = (unsigned)r * (unsigned)p.pitch + (unsigned)cA;
-                pinw = __ldg(p.pin_bits + (o >> 5)) >> (o & 31u);
+                pinword = __ldg(p.pin_bits + (o >> 5));
             }
         }
     };
-    float2 trN;
-    unsigned pinN;
-    row_inputs(r0, trN, pinN);
+    float2 trN = ws.trN;
+    unsigned pinN = ws.pinN;
 
     int r = r0 - 2;
     // the window's four row slots and the two slots of lane+1's pair
-    Node2 Pa = load_row(pin, r, p.ny, p.pitch, cmem);
-    Node2 Pb = load_row(pin, r + 1, p.ny, p.pitch, cmem);
-    Node2 Pc = load_row(pin, r + 2, p.ny, p.pitch, cmem);
+    Node2 Pa = load_row(in, st32, r, p.ny, p.pitch, cmem);
+    Node2 Pb = load_row(in, st32, r + 1, p.ny, p.pitch, cmem);
+    Node2 Pc = load_row(in, st32, r + 2, p.ny, p.pitch, cmem);
     Node2 Pd, Ne, Nf;
     // reactions sent into the next row by the rows above (springs (+1,0),
     // (+1,+1), (+1,-1) of row r-1 and (+2,0) of row r-2), and the (+2,0)
@@ -264,7 +274,7 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
     // row r (from the previous row); N1 receives lane+1's pair of row r+1.
     auto row = [&](auto phase, Node2 &P0, Node2 &P1, Node2 &P2, Node2 &P3, Node2 &N0, Node2 &N1) {
         constexpr int PH = decltype(phase)::value;
-        P3 = load_row(pin, r + 3, p.ny, p.pitch, cmem);  // prefetch
+        P3 = load_row(in, st32, r + 3, p.ny, p.pitch, cmem);  // prefetch
         Node2 M1;  // lane-1's B, row r+1 (.y only)
         if (PH >= 1) {
             N1.px = shfl_down2(P1.px, 1); N1.py = shfl_down2(P1.py, 1); N1.pz = shfl_down2(P1.pz, 1);
@@ -283,28 +293,40 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
             ksR = kdR = ksD = kdD = ksDR = kdDR = ksDL = kdDL = ksR2 = kdR2 = ksD2 = kdD2 = bc(0.0f);
             if (r >= 0 && r < p.ny && colmem) {
                 const unsigned o = (unsigned)r * (unsigned)p.pitch + (unsigned)cA;
-                const float *ks = p.ks_slot + o, *kd = p.kd_slot + o;
-                ksD2 = __ldg((const float2 *)(ks + 5 * st));
-                kdD2 = __ldg((const float2 *)(kd + 5 * st));
+                const float *ks = p.ks_slot, *kd = p.kd_slot;
+                ksD2 = __ldg((const float2 *)(ks + (o + 5u * st32)));
+                kdD2 = __ldg((const float2 *)(kd + (o + 5u * st32)));
                 if (PH >= 1) {
-                    ksD = __ldg((const float2 *)(ks + st));
-                    kdD = __ldg((const float2 *)(kd + st));
-                    ksDR = __ldg((const float2 *)(ks + 2 * st));
-                    kdDR = __ldg((const float2 *)(kd + 2 * st));
-                    ksDL = __ldg((const float2 *)(ks + 3 * st));
-                    kdDL = __ldg((const float2 *)(kd + 3 * st));
+                    ksD = __ldg((const float2 *)(ks + (o + st32)));
+                    kdD = __ldg((const float2 *)(kd + (o + st32)));
+                    ksDR = __ldg((const float2 *)(ks + (o + 2u * st32)));
+                    kdDR = __ldg((const float2 *)(kd + (o + 2u * st32)));
+                    ksDL = __ldg((const float2 *)(ks + (o + 3u * st32)));
+                    kdDL = __ldg((const float2 *)(kd + (o + 3u * st32)));
                 }
                 if (PH == 2) {
-                    ksR = __ldg((const float2 *)(ks));
-                    kdR = __ldg((const float2 *)(kd));
-                    ksR2 = __ldg((const float2 *)(ks + 4 * st));
-                    kdR2 = __ldg((const float2 *)(kd + 4 * st));
+                    ksR = __ldg((const float2 *)(ks + o));
+                    kdR = __ldg((const float2 *)(kd + o));
+                    ksR2 = __ldg((const float2 *)(ks + (o + 4u * st32)));
+                    kdR2 = __ldg((const float2 *)(kd + (o + 4u * st32)));
                 }
             }
         } else {
-            ksR = K.ksR; kdR = K.kdR; ksR2 = K.ksR2; kdR2 = K.kdR2;
-            ksD = K.ksD; kdD = K.kdD; ksD2 = K.ksD2; kdD2 = K.kdD2;
-            ksDR = K.ksDR; kdDR = K.kdDR; ksDL = K.ksDL; kdDL = K.kdDL;
+            ksR = ksD = bc(p.ks[0]);
+            kdR = kdD = bc(p.kd[0]);
+            ksDR = ksDL = bc(p.ks[1]);
+            kdDR = kdDL = bc(p.kd[1]);
+            ksR2 = ksD2 = bc(p.ks[2]);
+            kdR2 = kdD2 = bc(p.kd[2]);
+            if (edge_strip) {
+                const float2 mR = cmask(0), mR2 = cmask(2), mD = cmask(4), mDL = cmask(6);
+                ksR = mul2(ksR, mR); kdR = mul2(kdR, mR);
+                ksDR = mul2(ksDR, mR); kdDR = mul2(kdDR, mR);
+                ksR2 = mul2(ksR2, mR2); kdR2 = mul2(kdR2, mR2);
+                ksD = mul2(ksD, mD); kdD = mul2(kdD, mD);
+                ksD2 = mul2(ksD2, mD); kdD2 = mul2(kdD2, mD);
+                ksDL = mul2(ksDL, mDL); kdDL = mul2(kdDL, mDL);
+            }
             if (PH < 2) {
                 // halo rows above the grid own no springs
                 const float2 m0 = bc(r >= 0 ? 1.0f : 0.0f);
@@ -360,7 +382,7 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
 
         if (PH == 2) {
             const float2 tr = trN;
-            const unsigned pinw = pinN;
+            const unsigned pinw = pinN >> (((unsigned)r * (unsigned)p.pitch + (unsigned)cA) & 31u);
             row_inputs(r + 1, trN, pinN);
             // reactions arriving at this row from the left neighbours' springs
             Vec2 bR;  // right spring of (r, c-1): A <- lane-1's B, B <- own A
@@ -422,17 +444,16 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
                 fsum = add2(fsum, add2(add2(add2(xx, xy), add2(xz, wx)), add2(wy, wz)));
                 const unsigned o = (unsigned)r * (unsigned)p.pitch + (unsigned)cA;
                 if (p.vstar) {  // velocity after integration, before the response (adjoint recompute)
-                    float *vs = p.vstar + o;
-                    *(float2 *)(vs) = wx;
-                    *(float2 *)(vs + st) = wy;
-                    *(float2 *)(vs + 2 * st) = wz;
+                    *(float2 *)(p.vstar + o) = wx;
+                    *(float2 *)(p.vstar + (o + st32)) = wy;
+                    *(float2 *)(p.vstar + (o + 2u * st32)) = wz;
                 }
-                *(float2 *)(pout.k[0] + o) = xx;
-                *(float2 *)(pout.k[1] + o) = xy;
-                *(float2 *)(pout.k[2] + o) = xz;
-                *(float2 *)(pout.k[3] + o) = wx;
-                *(float2 *)(pout.k[4] + o) = wy;
-                *(float2 *)(pout.k[5] + o) = wz;
+                *(float2 *)(out + o) = xx;
+                *(float2 *)(out + (o + st32)) = xy;
+                *(float2 *)(out + (o + 2u * st32)) = xz;
+                *(float2 *)(out + (o + 3u * st32)) = wx;
+                *(float2 *)(out + (o + 4u * st32)) = wy;
+                *(float2 *)(out + (o + 5u * st32)) = wz;
             }
         }
         // reactions for the rows below
@@ -503,6 +524,12 @@ __global__ void CLOTH_WALK_BOUNDS substep_kernel(const StepParams p)
     __shared__ unsigned long long s_k;
     __shared__ float s_wbase;
     pdl_launch_dependents();
+    const int lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * WARPS_PER_CTA + (threadIdx.x >> 5);
+    const bool active = warp < p.strips_x * p.strips_y;
+    const int sx = active ? warp % p.strips_x : 0, sy = active ? warp / p.strips_x : 0;
+    WalkStatics ws{};
+    if (active) ws = walk_statics(p, sx, sy, lane);  // before the wait: static tables only
     pdl_wait();
     if (threadIdx.x == 0) {
         const unsigned long long k = *(volatile unsigned long long *)&p.ctrl->k;
@@ -515,12 +542,8 @@ __global__ void CLOTH_WALK_BOUNDS substep_kernel(const StepParams p)
     const unsigned long long k = s_k;
     const float *__restrict__ in = (k & 1ull) ? p.state1 : p.state0;
     float *__restrict__ out = (k & 1ull) ? p.state0 : p.state1;
-    const int lane = threadIdx.x & 31;
-    const int warp = blockIdx.x * WARPS_PER_CTA + (threadIdx.x >> 5);
     float2 fsum = bc(0.0f);  // sum of every stored value: non-finite iff one of them is
-    if (warp < p.strips_x * p.strips_y)
-        walk_strip<MESH, PER_SPRING>(p, in, out, s_wbase, warp % p.strips_x,
-                                     warp / p.strips_x, lane, 0, fsum);
+    if (active) walk_strip<MESH, PER_SPRING>(p, in, out, s_wbase, sx, sy, lane, 0, fsum, ws);
 
     const bool bad = !isfinite(fsum.x + fsum.y);
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
@@ -560,12 +583,13 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kern
 {
     __shared__ std::conditional_t<REC, CollSharedRec, CollShared> sh;
     __shared__ unsigned long long s_k;
-    __shared__ unsigned s_n;
+    __shared__ unsigned s_n, s_stat[2];
     pdl_launch_dependents();
     pdl_wait();
     if (threadIdx.x == 0) {
         s_k = *(volatile unsigned long long *)&p.ctrl->k;
         s_n = *(volatile unsigned *)p.coll_count;
+        s_stat[0] = s_stat[1] = 0u;
     }
     __syncthreads();
     const unsigned long long k = s_k;
@@ -577,10 +601,11 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kern
         return;
     }
     float fsum = 0.0f;
-    collide_list<REC>(OneClothList{p}, sh, k, s_n, fsum);
+    unsigned ntest = 0u, nhit = 0u;
+    collide_list<REC>(OneClothList{p}, sh, k, s_n, fsum, ntest, nhit);
     if (__any_sync(FULL, !isfinite(fsum)) && (threadIdx.x & 31) == 0)
         atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
-    __syncthreads();
+    coll_stats_add(p.ctrl, s_stat, s_n, ntest, nhit);
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(&p.ctrl->blocks_done, 1u);
         if (prev == gridDim.x - 1) {
@@ -681,12 +706,13 @@ __global__ void CLOTH_WALK_BOUNDS batch_substep_kernel(const BatchArgs b)
         const float wbase = p.has_wind ? (float)fmod(p.w_omega * (double)k + p.w_phase0, 6.283185307179586) : 0.0f;
         const float *in = (k & 1ull) ? p.state1 : p.state0;
         float *out = (k & 1ull) ? p.state0 : p.state1;
+        const WalkStatics ws = walk_statics(p, it.y, it.z, lane);
         if (p.has_mesh) {
-            if (p.ks_slot) walk_strip<true, true>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum);
-            else walk_strip<true, false>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum);
+            if (p.ks_slot) walk_strip<true, true>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum, ws);
+            else walk_strip<true, false>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum, ws);
         } else {
-            if (p.ks_slot) walk_strip<false, true>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum);
-            else walk_strip<false, false>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum);
+            if (p.ks_slot) walk_strip<false, true>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum, ws);
+            else walk_strip<false, false>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum, ws);
         }
         __syncwarp();  // the slot is rewritten by the next item
     }
@@ -719,20 +745,22 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) batch_collid
 {
     __shared__ CollShared sh;
     __shared__ unsigned long long s_k;
-    __shared__ unsigned s_n;
+    __shared__ unsigned s_n, s_stat[2];
     pdl_launch_dependents();
     pdl_wait();
     if (threadIdx.x == 0) {
         s_k = *(volatile unsigned long long *)&b.ctrl->k;
         s_n = *(volatile unsigned *)b.coll_count;
+        s_stat[0] = s_stat[1] = 0u;
     }
     __syncthreads();
     const unsigned long long k = s_k;
     float fsum = 0.0f;
-    collide_list(BatchList{b}, sh, k, s_n, fsum);
+    unsigned ntest = 0u, nhit = 0u;
+    collide_list(BatchList{b}, sh, k, s_n, fsum, ntest, nhit);
     if (__any_sync(FULL, !isfinite(fsum)) && (threadIdx.x & 31) == 0)
         atomicOr(&b.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
-    __syncthreads();
+    coll_stats_add(b.ctrl, s_stat, s_n, ntest, nhit);
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(&b.ctrl->blocks_done, 1u);
         if (prev == gridDim.x - 1) {
@@ -799,7 +827,7 @@ int substep_rows_per_warp(int nx, int ny, int sm_count)
     // fill a wave takes the shortest walks (128 x 128 with an icosphere, µs
     // per substep: R = 4 12.4, R = 2 10.0, R = 1 8.8)
     const long long strips_x = (nx + STRIP_COLS - 1) / STRIP_COLS;
-    const long long target = (long long)sm_count * WARPS_PER_CTA * CLOTH_WALK_MINB;
+    const long long target = (long long)sm_count * WARPS_PER_CTA * substep_min_ctas();
     long long strips_y = (target + strips_x - 1) / strips_x;
     long long R = (ny + strips_y - 1) / strips_y;
     if (R < 1) R = 1;
@@ -846,6 +874,7 @@ cudaError_t launch_walk(const StepParams &p, cudaStream_t s)
                : launch_k(substep_kernel<false, false>, blocks, threads, s, p);
 }
 
+
 cudaError_t launch_collide(const StepParams &p, cudaStream_t s)
 {
     if (p.edge_resp) {
@@ -873,7 +902,24 @@ cudaError_t launch_batch_substep(const BatchArgs &b, cudaStream_t s)
 
 int substep_strip_cols() { return STRIP_COLS; }
 int substep_warps_per_cta() { return WARPS_PER_CTA; }
-int substep_min_ctas() { return CLOTH_WALK_MINB; }
+// Resident CTAs per SM of the walk kernels (the smaller of the single-cloth
+// and batch kernels), from the occupancy calculator; looked up once.
+int substep_min_ctas()
+{
+    static int cached = 0;
+    if (cached > 0) return cached;
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, substep_kernel<true, false>, 32 * WARPS_PER_CTA, 0) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_substep_kernel, 32 * WARPS_PER_CTA, 0) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return CLOTH_WALK_MINB;
+    }
+    cached = a < b ? a : b;
+    if (cached < 1) cached = 1;
+    return cached;
+}
 
 cudaError_t launch_aos_to_soa(const float *aos_pos, const float *aos_vel, float *state0, float *state1,
                               long long stride, int n, int nx, int pitch, DevCtrl *ctrl, cudaStream_t s)

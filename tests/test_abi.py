@@ -138,10 +138,12 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
         A.lib()
 
 
-@pytest.mark.parametrize("nx,ny,what", [(1, 1 << 30, b"plane"), (1 << 16, 1 << 15, b"too many nodes")])
+@pytest.mark.parametrize("nx,ny,what", [(1, 1 << 30, b"plane"), (1 << 16, 1 << 15, b"too many nodes"),
+                                        (4, 1 << 28, b"32-bit state offsets")])
 def test_create_rejects_the_largest_grids_without_gpu(capi, nx, ny, what):
     # kernels index a plane with 32-bit offsets: a padded plane of 2^31 floats
-    # or more, or more than 2^30 nodes, is refused before any allocation
+    # or more, six planes of 2^32 floats or more, or more than 2^30 nodes, are
+    # refused before any allocation
     d = _desc(capi, nx=nx, ny=ny)
     h = C.c_void_p()
     assert capi.lib().cloth_create(C.byref(d), None, C.byref(h)) == capi.CLOTH_ERR_INVALID_ARG
