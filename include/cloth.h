@@ -75,10 +75,11 @@ enum {
  * triangles with the extended Moller-Trumbore test (Section 3); every vertex
  * of the cloth triangles sharing a hit edge moves from its previous position
  * towards the hit point, stopping contact_offset short, averaged over its
- * hits, and its velocity is scaled by restitution (Algorithm 2).  Nodes are
- * considered if their updated position lies within twice the rest diagonal of
- * the mesh's grid, so edges are assumed to stay under twice their rest length
- * within a substep.  Edges parallel to the surface are not detected (the
+ * hits, and its velocity is scaled by restitution (Algorithm 2).  A
+ * separate pass lists every node whose neighbourhood (its 3 x 3 block of
+ * nodes at the updated positions) has a box overlapping the mesh's grid, which
+ * holds every node of a triangle with an edge that can hit, however far the
+ * cloth is stretched.  Edges parallel to the surface are not detected (the
  * test's parallel rule).  Not accepted by cloth_batch_create or
  * cloth_rollout_create. */
 #define CLOTH_FLAG_EDGE_COLLISION 4u
@@ -282,7 +283,7 @@ int cloth_batch_set_state(ClothBatch *b, int32_t index, const float *pos, const 
  * fastest, and restores every cloth's state and the substep counter, so the
  * simulation is unchanged.  Synchronises. */
 int cloth_batch_tune(ClothBatch *b, int32_t trial_substeps, ClothBatchTuning *out);
-/* Set the tuning explicitly (rows_per_warp 1..64, walk_ctas_per_sm 1..32). */
+/* Set the tuning explicitly (rows_per_warp 1..32, walk_ctas_per_sm 1..32). */
 int cloth_batch_set_tuning(ClothBatch *b, int32_t rows_per_warp, int32_t walk_ctas_per_sm);
 int cloth_batch_get_tuning(ClothBatch *b, ClothBatchTuning *out);
 /* Wait for the batch's stream and report device-side error flags. */

@@ -160,13 +160,9 @@ void cloth_fill_params(ClothHandle *h)
     for (int a = 0; a < 3; a++) {
         // box of the non-border cells 1..dims-2 (border cells hold no triangle),
         // widened by 1% of a cell against rounding of the cell formula
-        // the edge narrow phase also needs the nodes of cloth triangles whose
-        // edges reach those cells: widen by twice the rest diagonal
-        const double m = (d.flags & CLOTH_FLAG_EDGE_COLLISION) ? 2.0 * (double)p.L0[2] : 0.0;
-        p.mlo[a] = h->has_mesh ? (float)((double)h->grid.origin[a] + 0.99 * (double)h->grid.h - m) : 0.0f;
-        p.mhi[a] = h->has_mesh
-                       ? (float)((double)h->grid.origin[a] + ((double)h->grid.dims[a] - 0.99) * h->grid.h + m)
-                       : 0.0f;
+        p.mlo[a] = h->has_mesh ? (float)((double)h->grid.origin[a] + 0.99 * (double)h->grid.h) : 0.0f;
+        p.mhi[a] = h->has_mesh ? (float)((double)h->grid.origin[a] + ((double)h->grid.dims[a] - 0.99) * h->grid.h)
+                               : 0.0f;
     }
     p.delta = d.contact_offset;
     p.eps = d.mt_eps;

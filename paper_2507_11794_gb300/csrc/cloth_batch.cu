@@ -191,7 +191,7 @@ int cloth_batch_create(const ClothDesc *descs, int32_t count, void *stream, Clot
         b->sm_count < 1)
         b->sm_count = 152;
     cudaGetLastError();
-    b->ctas_per_sm = substep_min_ctas();
+    b->ctas_per_sm = batch_min_ctas();
     long long total = 0;
     try {
         b->cl.reserve((size_t)count);
@@ -217,7 +217,7 @@ int cloth_batch_create(const ClothDesc *descs, int32_t count, void *stream, Clot
         strips_x_rows += (long long)((h->desc.nx + substep_strip_cols() - 1) / substep_strip_cols()) * h->desc.ny;
     const long long warps = (long long)b->sm_count * substep_warps_per_cta() * b->ctas_per_sm;
     long long R = (strips_x_rows + warps - 1) / warps;
-    b->rows_per_warp = (int)std::min<long long>(64, std::max<long long>(4, R));
+    b->rows_per_warp = (int)std::min<long long>(CLOTH_MAX_ROWS_PER_WARP, std::max<long long>(4, R));
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&b->ctrl, sizeof(DevCtrl));
     if (e == cudaSuccess) e = cudaMalloc(&b->work, sizeof(unsigned));
@@ -317,8 +317,9 @@ int cloth_batch_set_tuning(ClothBatch *b, int32_t rows_per_warp, int32_t walk_ct
 {
     int rc = check_batch(b);
     if (rc) return rc;
-    if (rows_per_warp < 1 || rows_per_warp > 64 || walk_ctas_per_sm < 1 || walk_ctas_per_sm > 32)
-        return bfail(CLOTH_ERR_INVALID_ARG, "rows_per_warp in [1,64], walk_ctas_per_sm in [1,32]");
+    if (rows_per_warp < 1 || rows_per_warp > CLOTH_MAX_ROWS_PER_WARP || walk_ctas_per_sm < 1 ||
+        walk_ctas_per_sm > 32)
+        return bfail(CLOTH_ERR_INVALID_ARG, "rows_per_warp in [1,32], walk_ctas_per_sm in [1,32]");
     b->rows_per_warp = rows_per_warp;
     b->ctas_per_sm = walk_ctas_per_sm;
     try {
@@ -351,7 +352,7 @@ int cloth_batch_tune(ClothBatch *b, int32_t trial_substeps, ClothBatchTuning *ou
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const int Rs[] = {4, 6, 8, 12, 16, 24, 32};
-    for (int c = 1; c <= substep_min_ctas() && e == cudaSuccess; c++)
+    for (int c = 1; c <= batch_min_ctas() && e == cudaSuccess; c++)
         for (int R : Rs) {
             if (e != cudaSuccess) break;
             b->rows_per_warp = R;

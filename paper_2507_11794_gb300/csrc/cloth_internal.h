@@ -18,6 +18,7 @@ struct DevCtrl {
     unsigned long long stat_listed, stat_tested, stat_hits;
 };
 
+// NONFINITE: a stored value was NaN/Inf; TIMEOUT: a bounded wait gave up
 enum : unsigned int { CTRL_FLAG_NONFINITE = 1u, CTRL_FLAG_TIMEOUT = 2u };
 
 // Spring directions (drow, dcol) of the canonical order; each node owns the
@@ -104,6 +105,9 @@ cudaError_t launch_batch_substep(const BatchArgs &b, cudaStream_t s);
 int substep_strip_cols();
 int substep_warps_per_cta();
 int substep_min_ctas();
+int batch_min_ctas();
+// Longest walk of one warp (rows); the walk marks rows in 32-bit masks.
+#define CLOTH_MAX_ROWS_PER_WARP 32
 // Rows per warp of the column walk for a grid and SM count; strips from it.
 int substep_rows_per_warp(int nx, int ny, int sm_count);
 void substep_shape(StepParams &p);

@@ -32,7 +32,7 @@ namespace {
 // Tuning knobs of the walk kernel (defaults chosen by measurement):
 // CTAs per SM the register budget targets, and the unroll of the row walk.
 #ifndef CLOTH_WALK_MINB
-#define CLOTH_WALK_MINB 2
+#define CLOTH_WALK_MINB 3
 #endif
 #ifndef CLOTH_WALK_UNROLL
 #define CLOTH_WALK_UNROLL 1
@@ -83,13 +83,44 @@ constexpr int WARPS_PER_CTA = CLOTH_WALK_WARPS;
 #else
 #define CLOTH_WALK_BOUNDS __launch_bounds__(32 * CLOTH_WALK_WARPS, CLOTH_WALK_MINB)
 #endif
+// the batch kernel (its walk also stages each item's parameters) keeps its own
+#ifndef CLOTH_BATCH_MINB
+#define CLOTH_BATCH_MINB 2
+#endif
 constexpr int STRIP_COLS = 60;
 
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// Packed FP32x2 arithmetic as explicitly rounded PTX instructions (add.rn,
+// mul.rn, fma.rn on .f32x2).  Each is one IEEE operation per component that
+// no optimizer fuses or reorders, so a node's arithmetic is the same whichever
+// copy of the unrolled row loop computes it; with the CUDA 13.0 packed
+// intrinsics (__fadd2_rn, __fmul2_rn, __ffma2_rn) the four copies of the loop
+// gave results one ulp apart, so a cloth's bits depended on its strip height.
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{.reg .b64 x, y, d;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\tadd.rn.f32x2 d, x, y;\n\t"
+        "mov.b64 {%0, %1}, d;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{.reg .b64 x, y, d;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\tmul.rn.f32x2 d, x, y;\n\t"
+        "mov.b64 {%0, %1}, d;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 r;
+    asm("{.reg .b64 x, y, z, d;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\tmov.b64 z, {%6, %7};\n\t"
+        "fma.rn.f32x2 d, x, y, z;\n\tmov.b64 {%0, %1}, d;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
 // a - b, exact as one rounding: fma(b, -1, a)
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return fma2(b, make_float2(-1.0f, -1.0f), a); }
 __device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
 
 struct Node2 {  // two nodes (A = .x, B = .y)
@@ -134,17 +165,34 @@ __device__ __forceinline__ Node2 load_row(const float *in, unsigned st, int r, i
 // d = q - p, F_p = (ks (|d| - L0) + kd (v_q - v_p).d / |d|) d / |d|, written
 // as F_p = s d with s = (ks (|d| - L0) + kd il (v_q - v_p).d) il, il = 1/|d|
 // (zero force for |d|^2 <= 1e-24).
-__device__ __forceinline__ Vec2 spring2(const Node2 &P, const Node2 &Q, float2 ks, float2 kd, float L0)
+// The same from the differences d = q - p (dx, dy, dz) and v_q - v_p (ux,
+// uy, uz).
+__device__ __forceinline__ Vec2 spring2d(float2 dx, float2 dy, float2 dz, float2 ux, float2 uy, float2 uz, float2 ks,
+                                         float2 kd, float L0)
 {
-    const float2 dx = sub2(Q.px, P.px), dy = sub2(Q.py, P.py), dz = sub2(Q.pz, P.pz);
     const float2 l2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
     float2 il;
     il.x = l2.x > 1e-24f ? rsqrtf(l2.x) : 0.0f;
     il.y = l2.y > 1e-24f ? rsqrtf(l2.y) : 0.0f;
-    const float2 dvd = fma2(sub2(Q.vz, P.vz), dz, fma2(sub2(Q.vy, P.vy), dy, mul2(sub2(Q.vx, P.vx), dx)));
+    const float2 dvd = fma2(uz, dz, fma2(uy, dy, mul2(ux, dx)));
     const float2 e = fma2(l2, il, bc(-L0));  // |d| - L0
     const float2 sc = mul2(fma2(mul2(kd, il), dvd, mul2(ks, e)), il);
     return {mul2(sc, dx), mul2(sc, dy), mul2(sc, dz)};
+}
+__device__ __forceinline__ Vec2 spring2(const Node2 &P, const Node2 &Q, float2 ks, float2 kd, float L0)
+{
+    return spring2d(sub2(Q.px, P.px), sub2(Q.py, P.py), sub2(Q.pz, P.pz), sub2(Q.vx, P.vx), sub2(Q.vy, P.vy),
+                    sub2(Q.vz, P.vz), ks, kd, L0);
+}
+// A spring of each node of the pair P towards the pair Q = (a.y, b.x) that
+// straddles two column pairs: the differences are formed one component at a
+// time, so Q is never assembled.
+__device__ __forceinline__ float2 dstr(float ay, float bx, float2 p) { return make_float2(__fsub_rn(ay, p.x), __fsub_rn(bx, p.y)); }
+__device__ __forceinline__ Vec2 spring2s(const Node2 &P, const Node2 &a, const Node2 &b, float2 ks, float2 kd,
+                                         float L0)
+{
+    return spring2d(dstr(a.px.y, b.px.x, P.px), dstr(a.py.y, b.py.x, P.py), dstr(a.pz.y, b.pz.x, P.pz),
+                    dstr(a.vx.y, b.vx.x, P.vx), dstr(a.vy.y, b.vy.x, P.vy), dstr(a.vz.y, b.vz.x, P.vz), ks, kd, L0);
 }
 
 __device__ __forceinline__ Vec2 vscale(Vec2 a, float2 s) { return {mul2(a.x, s), mul2(a.y, s), mul2(a.z, s)}; }
@@ -266,7 +314,7 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
     // (+1,+1), (+1,-1) of row r-1 and (+2,0) of row r-2), and the (+2,0)
     // reactions of row r-1 (they reach row r+1)
     Vec2 A1 = {}, D2p = {};
-    unsigned long long markA = 0ull, markB = 0ull;  // rows whose node needs the collision phase
+    unsigned markA = 0u, markB = 0u;  // rows (r - r0 < 32) whose node needs the collision phase
 
     // PH 0: row r0-2 (only its (+2,0) spring reaches an output row);
     // PH 1: row r0-1 (its (+1,*) and (+2,0) springs); PH 2: output rows.
@@ -335,65 +383,62 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
                 ksDR = mul2(ksDR, m0); kdDR = mul2(kdDR, m0);
                 ksDL = mul2(ksDL, m0); kdDL = mul2(kdDL, m0);
             }
+            if (r + 2 >= p.ny) {
+                // the grid's last two rows: no (+2,0) springs, and none of
+                // (+1,*) from the last row
+                const float2 m1 = bc(r + 1 < p.ny ? 1.0f : 0.0f);
+                ksD2 = kdD2 = bc(0.0f);
+                ksD = mul2(ksD, m1); kdD = mul2(kdD, m1);
+                ksDR = mul2(ksDR, m1); kdDR = mul2(kdDR, m1);
+                ksDL = mul2(ksDL, m1); kdDL = mul2(kdDL, m1);
+            }
         }
 
-        // the forward springs of the pair at row r
-        Vec2 fD2 = spring2(P0, P2, ksD2, kdD2, p.L0[5]);  // (+2,0)
-        Vec2 fD{}, fDR{}, fDL{}, fR{}, fR2{};
-        Node2 Q;
+        // the forward springs of the pair at row r; the node's own force is
+        // summed in the order they complete, and each reaction leaves for its
+        // receiving node as soon as it is known
+        const Vec2 fD2 = spring2(P0, P2, ksD2, kdD2, p.L0[5]);  // (+2,0): reaches row r+2
+        Vec2 own = fD2;
+        Vec2 A1n = D2p;  // reactions for row r+1
         if (PH >= 1) {
-            fD = spring2(P0, P1, ksD, kdD, p.L0[1]);  // (+1,0)
-            Q.px = make_float2(P1.px.y, N1.px.x); Q.py = make_float2(P1.py.y, N1.py.x);
-            Q.pz = make_float2(P1.pz.y, N1.pz.x); Q.vx = make_float2(P1.vx.y, N1.vx.x);
-            Q.vy = make_float2(P1.vy.y, N1.vy.x); Q.vz = make_float2(P1.vz.y, N1.vz.x);
-            fDR = spring2(P0, Q, ksDR, kdDR, p.L0[2]);  // (+1,+1)
-            Q.px = make_float2(M1.px.y, P1.px.x); Q.py = make_float2(M1.py.y, P1.py.x);
-            Q.pz = make_float2(M1.pz.y, P1.pz.x); Q.vx = make_float2(M1.vx.y, P1.vx.x);
-            Q.vy = make_float2(M1.vy.y, P1.vy.x); Q.vz = make_float2(M1.vz.y, P1.vz.x);
-            fDL = spring2(P0, Q, ksDL, kdDL, p.L0[3]);  // (+1,-1)
-        }
-        if (!PER_SPRING && PH >= 1 && r + 2 >= p.ny) {
-            // the grid's last two rows: no (+2,0) springs, and none of
-            // (+1,*) from the last row
-            const float2 m1 = bc(r + 1 < p.ny ? 1.0f : 0.0f);
-            fD2 = {};
-            fD = vscale(fD, m1);
-            fDR = vscale(fDR, m1);
-            fDL = vscale(fDL, m1);
-        }
-        if (PH == 2) {
-            Q.px = make_float2(P0.px.y, N0.px.x); Q.py = make_float2(P0.py.y, N0.py.x);
-            Q.pz = make_float2(P0.pz.y, N0.pz.x); Q.vx = make_float2(P0.vx.y, N0.vx.x);
-            Q.vy = make_float2(P0.vy.y, N0.vy.x); Q.vz = make_float2(P0.vz.y, N0.vz.x);
-            fR = spring2(P0, Q, ksR, kdR, p.L0[0]);      // (0,+1)
-            fR2 = spring2(P0, N0, ksR2, kdR2, p.L0[4]);  // (0,+2)
-        }
-        // diagonals of this row act on row r+1: A <- lane-1's B (down-right),
-        // B <- own A; A <- own B (down-left), B <- lane+1's A
-        Vec2 nDR{}, nDL{};
-        if (PH >= 1) {
+            const Vec2 fD = spring2(P0, P1, ksD, kdD, p.L0[1]);  // (+1,0)
+            own = vadd(own, fD);
+            A1n = vadd(A1n, fD);
+            const Vec2 fDR = spring2s(P0, P1, N1, ksDR, kdDR, p.L0[2]);  // (+1,+1): ends at (P1.y, N1.x)
+            own = vadd(own, fDR);
+            // down-right reactions for row r+1: A <- lane-1's B, B <- own A
+            Vec2 nDR;
             nDR.x = make_float2(__shfl_up_sync(FULL, fDR.x.y, 1), fDR.x.x);
             nDR.y = make_float2(__shfl_up_sync(FULL, fDR.y.y, 1), fDR.y.x);
             nDR.z = make_float2(__shfl_up_sync(FULL, fDR.z.y, 1), fDR.z.x);
+            A1n = vadd(A1n, nDR);
+            const Vec2 fDL = spring2s(P0, M1, P1, ksDL, kdDL, p.L0[3]);  // (+1,-1): ends at (M1.y, P1.x)
+            own = vadd(own, fDL);
+            // down-left reactions for row r+1: A <- own B, B <- lane+1's A
+            Vec2 nDL;
             nDL.x = make_float2(fDL.x.y, __shfl_down_sync(FULL, fDL.x.x, 1));
             nDL.y = make_float2(fDL.y.y, __shfl_down_sync(FULL, fDL.y.x, 1));
             nDL.z = make_float2(fDL.z.y, __shfl_down_sync(FULL, fDL.z.x, 1));
+            A1n = vadd(A1n, nDL);
         }
 
         if (PH == 2) {
             const float2 tr = trN;
             const unsigned pinw = pinN >> (((unsigned)r * (unsigned)p.pitch + (unsigned)cA) & 31u);
             row_inputs(r + 1, trN, pinN);
+            const Vec2 fR = spring2s(P0, P0, N0, ksR, kdR, p.L0[0]);  // (0,+1): ends at (P0.y, N0.x)
+            own = vadd(own, fR);
             // reactions arriving at this row from the left neighbours' springs
-            Vec2 bR;  // right spring of (r, c-1): A <- lane-1's B, B <- own A
-            bR.x = make_float2(__shfl_up_sync(FULL, fR.x.y, 1), fR.x.x);
-            bR.y = make_float2(__shfl_up_sync(FULL, fR.y.y, 1), fR.y.x);
-            bR.z = make_float2(__shfl_up_sync(FULL, fR.z.y, 1), fR.z.x);
-            const Vec2 bR2 = {shfl_up2(fR2.x, 1), shfl_up2(fR2.y, 1), shfl_up2(fR2.z, 1)};  // (r, c-2)
+            Vec2 back;  // right spring of (r, c-1): A <- lane-1's B, B <- own A
+            back.x = make_float2(__shfl_up_sync(FULL, fR.x.y, 1), fR.x.x);
+            back.y = make_float2(__shfl_up_sync(FULL, fR.y.y, 1), fR.y.x);
+            back.z = make_float2(__shfl_up_sync(FULL, fR.z.y, 1), fR.z.x);
+            const Vec2 fR2 = spring2(P0, N0, ksR2, kdR2, p.L0[4]);  // (0,+2)
+            own = vadd(own, fR2);
+            back = vadd(back, Vec2{shfl_up2(fR2.x, 1), shfl_up2(fR2.y, 1), shfl_up2(fR2.z, 1)});  // (r, c-2)
 
             // F = own forward springs - reactions of the springs that end here
-            const Vec2 own = vadd(vadd(vadd(fR, fR2), vadd(fD, fD2)), vadd(fDR, fDL));
-            const Vec2 F = vsub(own, vadd(A1, vadd(bR, bR2)));
+            const Vec2 F = vsub(own, vadd(A1, back));
 
             float2 ax = fma2(F.x, bc(p.inv_mass), bc(p.g[0]));
             float2 ay = fma2(F.y, bc(p.inv_mass), bc(p.g[1]));
@@ -434,8 +479,8 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
                                    fminf(P0.px.y, xx.y) <= p.mhi[0] && fmaxf(P0.py.y, xy.y) >= p.mlo[1] &&
                                    fminf(P0.py.y, xy.y) <= p.mhi[1] && fmaxf(P0.pz.y, xz.y) >= p.mlo[2] &&
                                    fminf(P0.pz.y, xz.y) <= p.mhi[2];
-                markA |= (unsigned long long)needA << (r - r0);
-                markB |= (unsigned long long)needB << (r - r0);
+                markA |= (unsigned)needA << (r - r0);
+                markB |= (unsigned)needB << (r - r0);
             }
             if (okA) {
                 if (!okB) {  // B is padding: keep it zero
@@ -457,7 +502,7 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
             }
         }
         // reactions for the rows below
-        if (PH >= 1) A1 = vadd(D2p, vadd(vadd(fD, nDR), nDL));
+        if (PH >= 1) A1 = A1n;
         D2p = fD2;
         r++;
     };
@@ -480,20 +525,17 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
     if (MESH) {
         // append the marked nodes to the collision list, row by row so that
         // consecutive entries are neighbouring columns
-        const unsigned long long mine = markA | markB;
-        const unsigned lo = __reduce_or_sync(FULL, (unsigned)mine);
-        const unsigned hi = __reduce_or_sync(FULL, (unsigned)(mine >> 32));
-        unsigned long long rows = ((unsigned long long)hi << 32) | lo;
-        const int cnt = __popcll(markA) + __popcll(markB);
+        unsigned rows = __reduce_or_sync(FULL, markA | markB);
+        const int cnt = __popc(markA) + __popc(markB);
         const int total = __reduce_add_sync(FULL, cnt);
         if (total > 0) {
             unsigned base = 0;
             if (lane == 0) base = atomicAdd(p.coll_count, (unsigned)total);
             base = __shfl_sync(FULL, base, 0);
             while (rows) {
-                const int b = __ffsll((long long)rows) - 1;
+                const int b = __ffs((int)rows) - 1;
                 rows &= rows - 1;
-                const int a = (int)((markA >> b) & 1ull), bb = (int)((markB >> b) & 1ull);
+                const int a = (int)((markA >> b) & 1u), bb = (int)((markB >> b) & 1u);
                 int inc = a + bb;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
@@ -518,7 +560,11 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
     }
 }
 
-template <bool MESH, bool PER_SPRING>
+// MESH: list the nodes near the surface model for the collision kernel,
+// which then ends the substep.  EDGE (the edge narrow phase): list nothing
+// (edge_list_kernel lists the nodes from the updated positions) and leave
+// the substep to that phase's kernels.
+template <bool MESH, bool PER_SPRING, bool EDGE = false>
 __global__ void CLOTH_WALK_BOUNDS substep_kernel(const StepParams p)
 {
     __shared__ unsigned long long s_k;
@@ -543,11 +589,11 @@ __global__ void CLOTH_WALK_BOUNDS substep_kernel(const StepParams p)
     const float *__restrict__ in = (k & 1ull) ? p.state1 : p.state0;
     float *__restrict__ out = (k & 1ull) ? p.state0 : p.state1;
     float2 fsum = bc(0.0f);  // sum of every stored value: non-finite iff one of them is
-    if (active) walk_strip<MESH, PER_SPRING>(p, in, out, s_wbase, sx, sy, lane, 0, fsum, ws);
+    if (active) walk_strip<MESH && !EDGE, PER_SPRING>(p, in, out, s_wbase, sx, sy, lane, 0, fsum, ws);
 
     const bool bad = !isfinite(fsum.x + fsum.y);
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
-    if (MESH) return;  // the collision kernel finishes the substep
+    if (MESH || EDGE) return;  // the collision kernels finish the substep
     __syncthreads();
     if (threadIdx.x == 0) {
         // the last CTA to finish advances the substep counter for the next launch
@@ -612,6 +658,65 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kern
             p.ctrl->blocks_done = 0;
             *p.coll_count = 0u;
             p.ctrl->k = k + 1;
+        }
+    }
+}
+
+// Listing of the edge narrow phase: every free node whose 3 x 3 block of
+// nodes at the updated positions (the walk's output) has a box that reaches
+// the box of the grid's inner cells.  A node is affected only through an
+// edge of one of its triangles, all of whose vertices lie in that block, and
+// such an edge can hit a triangle of the surface model only if its box meets
+// the grid's inner cells; so every node a hit can affect is listed, however
+// far the cloth is stretched.  One thread per node; appends are aggregated
+// per warp.
+__global__ void __launch_bounds__(256) edge_list_kernel(const __grid_constant__ StepParams p)
+{
+    __shared__ unsigned long long s_k;
+    pdl_launch_dependents();
+    pdl_wait();
+    if (threadIdx.x == 0) s_k = *(volatile unsigned long long *)&p.ctrl->k;
+    __syncthreads();
+    const unsigned long long k = s_k;
+    const float *xs = (k & 1ull) ? p.state0 : p.state1;  // updated positions
+    const long long st = p.stride;
+    const int lane = threadIdx.x & 31;
+    const long long n = (long long)p.nx * p.ny;
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < n; b += (long long)gridDim.x * blockDim.x) {
+        const long long i = b + threadIdx.x;
+        bool want = false;
+        int o = 0;
+        if (i < n) {
+            const int r = (int)(i / p.nx), c = (int)(i - (long long)r * p.nx);
+            o = r * p.pitch + c;
+            const bool pinned = p.pin_bits && ((__ldg(p.pin_bits + (o >> 5)) >> (o & 31)) & 1u);
+            if (!pinned) {
+                float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+                for (int dr = -1; dr <= 1; dr++) {
+                    const int rr = r + dr;
+                    if (rr < 0 || rr >= p.ny) continue;
+                    for (int dc = -1; dc <= 1; dc++) {
+                        const int cc = c + dc;
+                        if (cc < 0 || cc >= p.nx) continue;
+                        const int q = rr * p.pitch + cc;
+#pragma unroll
+                        for (int a = 0; a < 3; a++) {
+                            const float x = __ldg(xs + a * st + q);
+                            lo[a] = fminf(lo[a], x);
+                            hi[a] = fmaxf(hi[a], x);
+                        }
+                    }
+                }
+                want = lo[0] <= p.mhi[0] && hi[0] >= p.mlo[0] && lo[1] <= p.mhi[1] && hi[1] >= p.mlo[1] &&
+                       lo[2] <= p.mhi[2] && hi[2] >= p.mlo[2];
+            }
+        }
+        const unsigned m = __ballot_sync(FULL, want);
+        if (m) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(p.coll_count, (unsigned)__popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (want) p.coll_list[base + __popc(m & ((1u << lane) - 1u))] = o;
         }
     }
 }
@@ -681,7 +786,7 @@ __global__ void __launch_bounds__(256) edge_apply_kernel(const __grid_constant__
 // first), stages that cloth's parameters in its shared-memory slot and walks
 // the strip with the same code as the single-cloth kernel, so every cloth of a
 // batch gets exactly the arithmetic it gets when stepped alone.
-__global__ void CLOTH_WALK_BOUNDS batch_substep_kernel(const BatchArgs b)
+__global__ void __launch_bounds__(32 * CLOTH_WALK_WARPS, CLOTH_BATCH_MINB) batch_substep_kernel(const BatchArgs b)
 {
     __shared__ StepParams sp[WARPS_PER_CTA];
     __shared__ unsigned long long s_k;
@@ -822,7 +927,7 @@ int transfer_blocks(int n)
 
 int substep_rows_per_warp(int nx, int ny, int sm_count)
 {
-    // the resident warps of one wave (register-limited), walks of 1..64 rows;
+    // the resident warps of one wave (register-limited), walks of 1..32 rows;
     // a walk of R rows takes R + 2 row iterations, so a grid that does not
     // fill a wave takes the shortest walks (128 x 128 with an icosphere, µs
     // per substep: R = 4 12.4, R = 2 10.0, R = 1 8.8)
@@ -831,7 +936,7 @@ int substep_rows_per_warp(int nx, int ny, int sm_count)
     long long strips_y = (target + strips_x - 1) / strips_x;
     long long R = (ny + strips_y - 1) / strips_y;
     if (R < 1) R = 1;
-    if (R > 64) R = 64;
+    if (R > CLOTH_MAX_ROWS_PER_WARP) R = CLOTH_MAX_ROWS_PER_WARP;
     return (int)R;
 }
 
@@ -867,6 +972,9 @@ cudaError_t launch_walk(const StepParams &p, cudaStream_t s)
     const int blocks = (warps + WARPS_PER_CTA - 1) / WARPS_PER_CTA;
     const bool per = p.ks_slot != nullptr;
     const int threads = 32 * WARPS_PER_CTA;
+    if (p.has_mesh && p.edge_resp)
+        return per ? launch_k(substep_kernel<true, true, true>, blocks, threads, s, p)
+                   : launch_k(substep_kernel<true, false, true>, blocks, threads, s, p);
     if (p.has_mesh)
         return per ? launch_k(substep_kernel<true, true>, blocks, threads, s, p)
                    : launch_k(substep_kernel<true, false>, blocks, threads, s, p);
@@ -878,7 +986,9 @@ cudaError_t launch_walk(const StepParams &p, cudaStream_t s)
 cudaError_t launch_collide(const StepParams &p, cudaStream_t s)
 {
     if (p.edge_resp) {
-        cudaError_t e = launch_k(collide_edges_kernel, p.coll_blocks, 32 * COLL_WARPS, s, p);
+        cudaError_t e = launch_k(edge_list_kernel, p.coll_blocks, 256, s, p);
+        if (e != cudaSuccess) return e;
+        e = launch_k(collide_edges_kernel, p.coll_blocks, 32 * COLL_WARPS, s, p);
         if (e != cudaSuccess) return e;
         return launch_k(edge_apply_kernel, p.coll_blocks, 256, s, p);
     }
@@ -902,22 +1012,31 @@ cudaError_t launch_batch_substep(const BatchArgs &b, cudaStream_t s)
 
 int substep_strip_cols() { return STRIP_COLS; }
 int substep_warps_per_cta() { return WARPS_PER_CTA; }
-// Resident CTAs per SM of the walk kernels (the smaller of the single-cloth
-// and batch kernels), from the occupancy calculator; looked up once.
+// Resident CTAs per SM of the single-cloth walk kernel and of the batch walk
+// kernel, from the occupancy calculator; looked up once each.
+namespace {
+int occupancy(const void *kern, int fallback)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * WARPS_PER_CTA, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return fallback;
+    }
+    return n < 1 ? 1 : n;
+}
+}  // namespace
+
 int substep_min_ctas()
 {
     static int cached = 0;
-    if (cached > 0) return cached;
-    int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, substep_kernel<true, false>, 32 * WARPS_PER_CTA, 0) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_substep_kernel, 32 * WARPS_PER_CTA, 0) !=
-            cudaSuccess) {
-        cudaGetLastError();
-        return CLOTH_WALK_MINB;
-    }
-    cached = a < b ? a : b;
-    if (cached < 1) cached = 1;
+    if (cached <= 0) cached = occupancy((const void *)substep_kernel<true, false>, CLOTH_WALK_MINB);
+    return cached;
+}
+
+int batch_min_ctas()
+{
+    static int cached = 0;
+    if (cached <= 0) cached = occupancy((const void *)batch_substep_kernel, CLOTH_BATCH_MINB);
     return cached;
 }
 

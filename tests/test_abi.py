@@ -197,3 +197,11 @@ def test_static_grid_rejects_a_grid_over_the_cell_limit(capi):
     rc, prm, msg = _static_reject(capi, verts, tris)
     assert rc == capi.CLOTH_ERR_INVALID_ARG and b"cells exceeds the static limit" in msg
     assert prm.ncells > 262144 and prm.ncells == prm.dims[0] * prm.dims[1] * prm.dims[2]
+
+
+def test_status_codes_match_the_header(capi):
+    src = open(HEADER).read()
+    codes = dict((n, int(v)) for n, v in re.findall(r"\bCLOTH_(OK|ERR_\w+)\s*=\s*(-?\d+)", src))
+    assert codes["OK"] == 0 and len(codes) >= 8
+    for name, val in codes.items():
+        assert getattr(capi, "CLOTH_" + name) == val, name

@@ -69,7 +69,7 @@ def test_tuning_leaves_the_simulation_unchanged(cloth_lib):
         a.step(3)
         b.step(3)
         t = b.tune(4)
-        assert t.candidates >= 7 and 1 <= t.rows_per_warp <= 64 and t.us_per_substep > 0
+        assert t.candidates >= 7 and 1 <= t.rows_per_warp <= 32 and t.us_per_substep > 0
         assert b.tuning().rows_per_warp == t.rows_per_warp
         a.step(5)
         b.step(5)

@@ -80,3 +80,36 @@ def test_edge_mode_is_rejected_by_the_rollout(cloth_lib):
         ro = C.c_void_p()
         rc = cloth_lib.capi.lib().cloth_rollout_create(C.c_void_p(cl.h), 4, 2, C.byref(ro))
         assert rc == cloth_lib.capi.CLOTH_ERR_INVALID_ARG
+
+
+def test_edge_phase_lists_the_nodes_of_stretched_edges(cloth_lib, oracle_lib):
+    # The paper's response moves a node towards a hit point on another edge of
+    # its triangles, so in contact the cloth's edges can stretch to several
+    # rest diagonals (up to 7 in the FP64 oracle on the sphere scene).  Here
+    # one node sits 0.3 m below a floor and its neighbours 0.3 m above, far
+    # outside any fixed margin around the floor, with the edges between them
+    # crossing it.  The listing from the updated positions must still find
+    # every node a hit affects: one substep matches the oracle, which tests
+    # every edge of the cloth.
+    # (placed so that no edge crosses the floor near the diagonal its two
+    # triangles share, where a float32 and a double test can differ)
+    nx = ny = 9
+    sc = make_scene(nx, ny, origin=(0.213, 0.3, 0.2), du=(0.02, 0, 0), dv=(0, 0, 0.02), total_mass=0.2,
+                    ks=(20.0, 10.0, 4.0), kd=(0.02, 0.02, 0.01), gravity=(0, -9.81, 0), dt=1 / 4800, substeps=1,
+                    mesh=floor_mesh(), delta=1e-4)
+    pos = sc.init_pos.copy()
+    pos[4 * nx + 4, 1] = -0.3
+    vel = np.zeros_like(pos)
+    cl = oracle_lib.Cloth(sc)
+    grid = oracle_lib.Grid(sc.mesh_verts, sc.mesh_tris)
+    xo, _, hits = oracle_lib.step_edges(cl, pos, vel, 0, 1, grid, want_hits=True)
+    affected = np.nonzero(hits > 0)[0]
+    assert len(affected) >= 4  # the neighbours of the low node
+    far = affected[affected != 4 * nx + 4]
+    assert np.all(pos[far, 1] > 0.25)  # 0.25 m or more above the floor
+    with cloth_lib.Cloth(sc, flags=_edge(cloth_lib)) as g:
+        g.set_state(pos, vel)
+        g.step(1)
+        p, _ = g.read()
+    err = np.abs(p.astype(np.float64) - xo).max()
+    assert err <= 1e-5, err
