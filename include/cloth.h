@@ -184,10 +184,12 @@ int cloth_sync(ClothHandle *h);
 /* Running totals of the collision phase since create, summed over substeps
  * (not part of the paper, which gives no counts; they describe the work of
  * the grid broad phase and narrow phase of Section 3): listed = nodes whose
- * substep path box reached the surface model's grid, tested = candidate
- * triangles put through the extended Moller-Trumbore test, hits = nodes that
- * received a response.  Zero without a surface model, and not counted by
- * the edge narrow phase (CLOTH_FLAG_EDGE_COLLISION).  Synchronises.  Any
+ * substep path box reached the surface model's (padded) bounding box,
+ * tested = candidate triangles put through the extended Moller-Trumbore
+ * test, hits = nodes that received a response.  With the edge narrow phase
+ * (CLOTH_FLAG_EDGE_COLLISION): listed = nodes whose 3 x 3 block box reached
+ * that box, tested = candidate triangles of their owned edges, hits = edges
+ * with at least one hit.  Zero without a surface model.  Synchronises.  Any
  * output may be NULL.  Errors: CLOTH_ERR_INVALID_ARG, CLOTH_ERR_STATE,
  * CLOTH_ERR_CUDA. */
 int cloth_get_collision_stats(ClothHandle *h, int64_t *listed, int64_t *tested, int64_t *hits);

@@ -84,6 +84,12 @@ void free_all(ClothHandle *h)
     h->force = nullptr;
     cudaFree(h->edge_resp);
     h->edge_resp = nullptr;
+    cudaFree(h->edge_hit);
+    h->edge_hit = nullptr;
+    cudaFree(h->edge_stamp);
+    h->edge_stamp = nullptr;
+    cudaFree(h->edge_more);
+    h->edge_more = nullptr;
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->state = nullptr;
     h->pin_bits = nullptr;
@@ -157,12 +163,16 @@ void cloth_fill_params(ClothHandle *h)
         p.gd[a] = h->grid.dims[a];
     }
     p.ginv = h->grid.inv;
+    // nodes whose path box reaches the box of the mesh's vertices are listed for
+    // the narrow phase (a path outside it meets no triangle); the box is padded
+    // by 1e-4 of its largest side, far above float32 rounding of the test
+    double ext = 0.0;
+    for (int a = 0; a < 3; a++)
+        if (h->has_mesh) ext = fmax(ext, (double)h->grid.hi[a] - (double)h->grid.lo[a]);
+    const double pad = 1e-4 * ext + 1e-6;
     for (int a = 0; a < 3; a++) {
-        // box of the non-border cells 1..dims-2 (border cells hold no triangle),
-        // widened by 1% of a cell against rounding of the cell formula
-        p.mlo[a] = h->has_mesh ? (float)((double)h->grid.origin[a] + 0.99 * (double)h->grid.h) : 0.0f;
-        p.mhi[a] = h->has_mesh ? (float)((double)h->grid.origin[a] + ((double)h->grid.dims[a] - 0.99) * h->grid.h)
-                               : 0.0f;
+        p.mlo[a] = h->has_mesh ? (float)((double)h->grid.lo[a] - pad) : 0.0f;
+        p.mhi[a] = h->has_mesh ? (float)((double)h->grid.hi[a] + pad) : 0.0f;
     }
     p.delta = d.contact_offset;
     p.eps = d.mt_eps;
@@ -171,6 +181,9 @@ void cloth_fill_params(ClothHandle *h)
     p.ctrl = h->ctrl;
     p.force = h->force;
     p.edge_resp = h->edge_resp;
+    p.edge_hit = h->edge_hit;
+    p.edge_stamp = h->edge_stamp;
+    p.edge_more = h->edge_more;
     p.coll_list = h->coll_list;
     p.coll_count = h->ctrl ? &h->ctrl->coll_count : nullptr;
     p.coll_blocks = h->sm_count * CLOTH_COLL_CTAS_PER_SM;
@@ -338,9 +351,16 @@ int cloth_create(const ClothDesc *desc, void *stream, ClothHandle **out)
                     break;
             }
         }
-        if ((d.flags & CLOTH_FLAG_EDGE_COLLISION) &&
-            (e = cudaMalloc(&h->edge_resp, sizeof(float4) * (size_t)N)) != cudaSuccess)
-            break;
+        if (d.flags & CLOTH_FLAG_EDGE_COLLISION) {
+            if ((e = cudaMalloc(&h->edge_resp, sizeof(float4) * (size_t)N)) != cudaSuccess) break;
+            if ((e = cudaMalloc(&h->edge_hit, sizeof(float4) * 3 * (size_t)h->stride)) != cudaSuccess) break;
+            if ((e = cudaMalloc(&h->edge_more, sizeof(float4) * CLOTH_EDGE_MORE * 3 * (size_t)h->stride)) !=
+                cudaSuccess)
+                break;
+            if ((e = cudaMalloc(&h->edge_stamp, sizeof(unsigned long long) * (size_t)h->stride)) != cudaSuccess) break;
+            if ((e = cudaMemsetAsync(h->edge_stamp, 0, sizeof(unsigned long long) * (size_t)h->stride, h->stream)) != cudaSuccess)
+                break;
+        }
         if (d.flags & CLOTH_FLAG_ATOMIC_SPRINGS) {
             const size_t nf = (size_t)h->pitch * d.ny;
             if ((e = cudaMalloc(&h->force, sizeof(float4) * nf)) != cudaSuccess) break;
@@ -420,6 +440,16 @@ int cloth_set_mesh(ClothHandle *h, const float *verts, int32_t nverts, const int
     if (ntris > 0) {
         if (grid_params(verts, tris, ntris, &g.h, g.origin, g.dims, &g.inv) != 0)
             return fail(CLOTH_ERR_BAD_MESH, "grid parameters");
+        for (int a = 0; a < 3; a++) {
+            g.lo[a] = INFINITY;
+            g.hi[a] = -INFINITY;
+        }
+        for (long long i = 0; i < 3 * (long long)ntris; i++)
+            for (int a = 0; a < 3; a++) {
+                const float x = verts[3 * (long long)tris[i] + a];
+                g.lo[a] = fminf(g.lo[a], x);
+                g.hi[a] = fmaxf(g.hi[a], x);
+            }
         float *dv = nullptr;
         int *dt = nullptr;
         cudaError_t e = cudaMalloc(&dv, sizeof(float) * 3 * (size_t)nverts);

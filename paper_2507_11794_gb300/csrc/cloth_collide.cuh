@@ -71,6 +71,13 @@ __device__ __forceinline__ bool coll_candidate(const StepParams &p, const CollPa
     return th > p.tmin && th < q.L;
 }
 
+// Point S + th r of a path, each coordinate one rounded fused multiply-add,
+// so every kernel that computes a hit point gets the same bits.
+__device__ __forceinline__ float3 coll_hit_point(const CollPath &q, float th)
+{
+    return make_float3(__fmaf_rn(th, q.rx, q.sx), __fmaf_rn(th, q.ry, q.sy), __fmaf_rn(th, q.rz, q.sz));
+}
+
 // Path of S -> E; false when it is shorter than eps (no test).
 __device__ __forceinline__ bool coll_path(const StepParams &p, float sx, float sy, float sz, float ex, float ey,
                                           float ez, CollPath &q)
@@ -134,7 +141,7 @@ __device__ __forceinline__ bool collide_t(const StepParams &p, float sx, float s
 }
 
 // ------------------------------------------------- cooperative list pass
-// The walk appends the nodes whose path box meets the grid's inner cells.
+// The walk appends the nodes whose path box meets the box of the mesh's vertices.
 // Most of them find empty cells; the few next to the surface find about a
 // dozen candidates each, and those sit next to one another in the list.  One
 // thread per node would leave those few threads testing their candidates one
@@ -422,6 +429,9 @@ __device__ __forceinline__ EdgeOfs edge_of_node(int q)
     }
 }
 constexpr int EDGES_PER_NODE = 12;
+// Hits after an edge's first whose points pass A stores (p.edge_more); pass B
+// walks an edge with more hits than 1 + EDGE_MORE again.
+constexpr int EDGE_MORE = CLOTH_EDGE_MORE;
 
 struct EdgeShared {
     CollLane lane[COLL_WARPS][32];
@@ -429,141 +439,326 @@ struct EdgeShared {
     float4 hit[COLL_WARPS][32];  // one round's results: hit point P and 1, or w = 0
 };
 
-// One warp's pass over 32 list entries per round; writes the response of
-// entry i to p.edge_resp[i] as (position, 1) or (0, 0, 0, 0) without a hit.
-__device__ __forceinline__ void collide_edges_list(const StepParams &p, EdgeShared &sh, unsigned long long k,
-                                                   unsigned n)
+// The kind of the triangulation edge from (ra, ca) to (rb, cb): 0 (0,+1),
+// 1 (+1,0), 2 (+1,+1).
+__device__ __forceinline__ int edge_kind(int ra, int ca, int rb, int cb) { return rb == ra ? 0 : (cb == ca ? 1 : 2); }
+
+// The first hit point of an edge path and its number of hits, walked by the
+// whole warp (every lane passes the same path and box; call from converged
+// code): the box's cells 32 at a time, x fastest, and each chunk's candidates
+// 32 at a time in cell order, so the first hit and the count are those of a
+// walk over the candidates in order.  Returns the same record on every lane
+// and adds the candidates tested to ntest.
+__device__ __forceinline__ float4 edge_hits_warp(const StepParams &p, const CollPath &path, const CollBox &bx,
+                                                 long long slot, int lane, unsigned &ntest)
+{
+    constexpr unsigned FULLW = 0xffffffffu;
+    const int nxc = bx.hix - bx.lox + 1, nyc = bx.hiy - bx.loy + 1, nzc = bx.hiz - bx.loz + 1;
+    const long long nxy = (long long)nxc * nyc, ncell = nxy * nzc;
+    float4 rec = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (long long c0 = 0; c0 < ncell; c0 += 32) {
+        const long long cc = c0 + lane;
+        int e0 = 0, cnt = 0, cx = 0, cy = 0, cz = 0;
+        if (cc < ncell) {
+            cz = bx.loz + (int)(cc / nxy);
+            const int rem = (int)(cc - (long long)(cz - bx.loz) * nxy);
+            cy = bx.loy + rem / nxc;
+            cx = bx.lox + rem % nxc;
+            const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
+            e0 = __ldg(p.cell_start + cell);
+            cnt = __ldg(p.cell_start + cell + 1) - e0;
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(FULLW, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const int total = __shfl_sync(FULLW, incl, 31);
+        const int excl = incl - cnt;
+        ntest += (unsigned)total;
+        for (int r0 = 0; r0 < total; r0 += 32) {
+            const int j = r0 + lane;
+            // the lane whose cell holds candidate j: the last with excl <= j
+            int ow = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(FULLW, excl, ow + step) <= j) ow += step;
+            const int oe0 = __shfl_sync(FULLW, e0, ow), oex = __shfl_sync(FULLW, excl, ow);
+            const int ocx = __shfl_sync(FULLW, cx, ow), ocy = __shfl_sync(FULLW, cy, ow),
+                      ocz = __shfl_sync(FULLW, cz, ow);
+            bool hit = false;
+            float th = 0.0f;
+            if (j < total) {
+                float f;
+                float4 A, B, C;
+                hit = coll_candidate(p, path, (long long)oe0 + (j - oex), ocx, ocy, ocz, bx.lox, bx.loy, bx.loz, th,
+                                     f, A, B, C);
+            }
+            const unsigned hm = __ballot_sync(FULLW, hit);
+            if (hm) {
+                const float3 hp = coll_hit_point(path, th);
+                const float hx = hp.x, hy = hp.y, hz = hp.z;
+                // this lane's hit is number rank (from 0) of the edge
+                const int rank = (int)rec.w + __popc(hm & ((1u << lane) - 1u));
+                if (hit && rank >= 1 && rank <= EDGE_MORE)
+                    p.edge_more[(long long)(rank - 1) * 3 * p.stride + slot] = make_float4(hx, hy, hz, 1.0f);
+                if (rec.w == 0.0f) {
+                    const int src = __ffs(hm) - 1;
+                    rec = make_float4(__shfl_sync(FULLW, hx, src), __shfl_sync(FULLW, hy, src),
+                                      __shfl_sync(FULLW, hz, src), 0.0f);
+                }
+                rec.w += (float)__popc(hm);
+            }
+        }
+    }
+    return rec;
+}
+
+// Pass A of the edge narrow phase: every listed node tests the three edges it
+// owns, (0,+1), (+1,0) and (+1,+1) from it (the triangulation's edges,
+// oriented from their upper-left endpoint), at the updated positions, so each
+// edge is tested once.  32 edges per warp and round, their candidates spread
+// over the lanes as in the node pass; an edge whose box spans more than
+// COLL_MAXC cells is walked afterwards by the whole warp (edge_hits_warp).
+// Records per edge its first hit point (in candidate order) and its number of
+// hits, p.edge_hit[kind * stride + owner] = (P, K), and the points of its hits
+// 2 .. 1 + EDGE_MORE at p.edge_more[(h - 2) * 3 * stride + kind * stride +
+// owner].  Counts the lane's tested candidates and edges that hit into ntest
+// and nhit.
+__device__ __forceinline__ void edge_test_list(const StepParams &p, EdgeShared &sh, unsigned long long k, unsigned n,
+                                               unsigned &ntest, unsigned &nhit)
 {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned long long nw = (unsigned long long)gridDim.x * COLL_WARPS;
     const unsigned long long w = (unsigned long long)blockIdx.x * COLL_WARPS + wib;
     CollLane &me = sh.lane[wib][lane];
     const long long st = p.stride;
-    const float *in = (k & 1ull) ? p.state1 : p.state0;
     const float *xs = (k & 1ull) ? p.state0 : p.state1;  // updated positions (written by the walk)
-    for (unsigned long long b0 = 0; b0 < n; b0 += 32ull * nw) {
-        const unsigned long long i = b0 + (unsigned long long)lane * nw + w;
-        const bool valid = i < n;
-        int r = 0, c = 0;
-        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-        if (valid) {
-            const int o = __ldg(p.coll_list + i);
-            r = o / p.pitch;
-            c = o - r * p.pitch;
-            sx = __ldg(in + o);
-            sy = __ldg(in + st + o);
-            sz = __ldg(in + 2 * st + o);
-        }
-        float ax = 0.0f, ay = 0.0f, az = 0.0f;  // sum of directions
-        int K = 0;
-        for (int q = 0; q < EDGES_PER_NODE; q++) {
-            int cnt = 0;
-            if (valid) {
-                const EdgeOfs e = edge_of_node(q);
-                const int ra = r + e.ar, ca = c + e.ac, rb = r + e.br, cb = c + e.bc;
-                if (ra >= 0 && ca >= 0 && rb < p.ny && cb < p.nx && ca < p.nx && cb >= 0) {
-                    const long long oa = (long long)ra * p.pitch + ca, ob = (long long)rb * p.pitch + cb;
-                    const float x0 = xs[oa], y0 = xs[st + oa], z0 = xs[2 * st + oa];
-                    const float x1 = xs[ob], y1 = xs[st + ob], z1 = xs[2 * st + ob];
-                    CollPath path;
-                    if (coll_path(p, x0, y0, z0, x1, y1, z1, path)) {
-                        const CollBox bx = coll_box(p, x0, y0, z0, x1, y1, z1);
-                        const int nxc = bx.hix - bx.lox + 1, nyc = bx.hiy - bx.loy + 1, nzc = bx.hiz - bx.loz + 1;
-                        if ((long long)nxc * nyc * nzc <= COLL_MAXC) {
-                            int cc = 0;
-                            for (int cz = bx.loz; cz <= bx.hiz; cz++)
-                                for (int cy = bx.loy; cy <= bx.hiy; cy++)
-                                    for (int cx = bx.lox; cx <= bx.hix; cx++, cc++) {
-                                        const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
-                                        const int e0 = __ldg(p.cell_start + cell), e1 = __ldg(p.cell_start + cell + 1);
-                                        cnt += e1 - e0;
-                                        me.cell[cc] = make_int2(e0, cnt);
-                                    }
-                            me.s = make_float4(path.sx, path.sy, path.sz, path.L);
-                            me.r = make_float4(path.rx, path.ry, path.rz, 0.0f);
-                            me.box = make_int4(bx.lox, bx.loy, bx.loz, nxc | (nyc << 16));
-                        } else {
-                            // an edge spanning more than COLL_MAXC cells: this lane
-                            // walks its candidates alone, in the same order
-                            for (int cz = bx.loz; cz <= bx.hiz; cz++)
-                                for (int cy = bx.loy; cy <= bx.hiy; cy++)
-                                    for (int cx = bx.lox; cx <= bx.hix; cx++) {
-                                        const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
-                                        const int e0 = __ldg(p.cell_start + cell), e1 = __ldg(p.cell_start + cell + 1);
-                                        for (int ee = e0; ee < e1; ee++) {
-                                            float th, f;
-                                            float4 A, B, C;
-                                            if (!coll_candidate(p, path, ee, cx, cy, cz, bx.lox, bx.loy, bx.loz, th, f,
-                                                                A, B, C))
-                                                continue;
-                                            const float wx = path.sx + th * path.rx - sx;
-                                            const float wy = path.sy + th * path.ry - sy;
-                                            const float wz = path.sz + th * path.rz - sz;
-                                            const float lw = sqrtf(wx * wx + wy * wy + wz * wz);
-                                            const float sc = lw > 0.0f ? fmaxf(lw - p.delta, 0.0f) / lw : 0.0f;
-                                            ax += sc * wx;
-                                            ay += sc * wy;
-                                            az += sc * wz;
-                                            K++;
-                                        }
-                                    }
-                        }
+    const unsigned long long items = 3ull * n;
+    for (unsigned long long b0 = 0; b0 < items; b0 += 32ull * nw) {
+        const unsigned long long j = b0 + (unsigned long long)lane * nw + w;
+        int cnt = 0;
+        bool has = false, wide = false;
+        long long slot = 0;
+        float4 rec = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        CollPath path = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        CollBox bx = {0, 0, 0, 0, 0, 0};
+        if (j < items) {
+            const int q = (int)(j % 3ull);
+            const int o = __ldg(p.coll_list + j / 3ull);
+            const int r = o / p.pitch, c = o - r * p.pitch;
+            const int rb = r + (q >= 1 ? 1 : 0), cb = c + (q != 1 ? 1 : 0);
+            if (rb < p.ny && cb < p.nx) {
+                has = true;
+                slot = (long long)q * st + o;
+                const long long ob = (long long)rb * p.pitch + cb;
+                const float x0 = xs[o], y0 = xs[st + o], z0 = xs[2 * st + o];
+                const float x1 = xs[ob], y1 = xs[st + ob], z1 = xs[2 * st + ob];
+                if (coll_path(p, x0, y0, z0, x1, y1, z1, path)) {
+                    bx = coll_box(p, x0, y0, z0, x1, y1, z1);
+                    const int nxc = bx.hix - bx.lox + 1, nyc = bx.hiy - bx.loy + 1, nzc = bx.hiz - bx.loz + 1;
+                    if ((long long)nxc * nyc * nzc <= COLL_MAXC) {
+                        int cc = 0;
+                        for (int cz = bx.loz; cz <= bx.hiz; cz++)
+                            for (int cy = bx.loy; cy <= bx.hiy; cy++)
+                                for (int cx = bx.lox; cx <= bx.hix; cx++, cc++) {
+                                    const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
+                                    const int e0 = __ldg(p.cell_start + cell), e1 = __ldg(p.cell_start + cell + 1);
+                                    cnt += e1 - e0;
+                                    me.cell[cc] = make_int2(e0, cnt);
+                                }
+                        me.s = make_float4(path.sx, path.sy, path.sz, path.L);
+                        me.r = make_float4(path.rx, path.ry, path.rz, 0.0f);
+                        me.box = make_int4(bx.lox, bx.loy, bx.loz, nxc | (nyc << 16));
+                    } else {
+                        wide = true;
                     }
                 }
             }
-            int incl = cnt;
+        }
+        int incl = cnt;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += t;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int excl = incl - cnt;
+        sh.base[wib][lane] = excl;
+        __syncwarp();
+        for (int r0 = 0; r0 < total; r0 += 32) {
+            const int jj = r0 + lane;
+            float4 hv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (jj < total) {
+                int ow = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (sh.base[wib][ow + step] <= jj) ow += step;
+                const CollLane &L = sh.lane[wib][ow];
+                const int loc = jj - sh.base[wib][ow];
+                int cc = 0;
+                while (L.cell[cc].y <= loc) cc++;
+                const long long e = L.cell[cc].x + (loc - (cc ? L.cell[cc - 1].y : 0));
+                const int nxc = L.box.w & 0xffff, nyc = L.box.w >> 16;
+                const int cx = L.box.x + cc % nxc, cy = L.box.y + (cc / nxc) % nyc, cz = L.box.z + cc / (nxc * nyc);
+                const CollPath lq = {L.s.x, L.s.y, L.s.z, L.r.x, L.r.y, L.r.z, L.s.w};
+                float th, f;
+                float4 A, B, C;
+                if (coll_candidate(p, lq, e, cx, cy, cz, L.box.x, L.box.y, L.box.z, th, f, A, B, C)) {
+                    const float3 hp = coll_hit_point(lq, th);
+                    hv = make_float4(hp.x, hp.y, hp.z, 1.0f);
+                }
             }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            const int excl = incl - cnt;
-            sh.base[wib][lane] = excl;
+            sh.hit[wib][lane] = hv;
             __syncwarp();
-            for (int r0 = 0; r0 < total; r0 += 32) {
-                const int j = r0 + lane;
-                float4 hv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (j < total) {
-                    int ow = 0;
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1)
-                        if (sh.base[wib][ow + step] <= j) ow += step;
-                    const CollLane &L = sh.lane[wib][ow];
-                    const int loc = j - sh.base[wib][ow];
-                    int cc = 0;
-                    while (L.cell[cc].y <= loc) cc++;
-                    const long long e = L.cell[cc].x + (loc - (cc ? L.cell[cc - 1].y : 0));
-                    const int nxc = L.box.w & 0xffff, nyc = L.box.w >> 16;
-                    const int cx = L.box.x + cc % nxc, cy = L.box.y + (cc / nxc) % nyc, cz = L.box.z + cc / (nxc * nyc);
-                    const CollPath lq = {L.s.x, L.s.y, L.s.z, L.r.x, L.r.y, L.r.z, L.s.w};
+            if (cnt > 0) {
+                const int q0 = max(excl, r0), q1 = min(excl + cnt, r0 + 32);
+                for (int t = q0; t < q1; t++) {
+                    const float4 P = sh.hit[wib][t - r0];
+                    if (P.w == 0.0f) continue;
+                    if (rec.w == 0.0f) rec = make_float4(P.x, P.y, P.z, 0.0f);
+                    else if (rec.w <= (float)EDGE_MORE) p.edge_more[(long long)(rec.w - 1.0f) * 3 * st + slot] = P;
+                    rec.w += 1.0f;
+                }
+            }
+            __syncwarp();
+        }
+        // the wide edges of this round, one at a time over the whole warp
+        for (unsigned wm = __ballot_sync(0xffffffffu, wide); wm; wm &= wm - 1u) {
+            const int src = __ffs(wm) - 1;
+            const CollPath q = {__shfl_sync(0xffffffffu, path.sx, src), __shfl_sync(0xffffffffu, path.sy, src),
+                                __shfl_sync(0xffffffffu, path.sz, src), __shfl_sync(0xffffffffu, path.rx, src),
+                                __shfl_sync(0xffffffffu, path.ry, src), __shfl_sync(0xffffffffu, path.rz, src),
+                                __shfl_sync(0xffffffffu, path.L, src)};
+            const CollBox b = {__shfl_sync(0xffffffffu, bx.lox, src), __shfl_sync(0xffffffffu, bx.loy, src),
+                               __shfl_sync(0xffffffffu, bx.loz, src), __shfl_sync(0xffffffffu, bx.hix, src),
+                               __shfl_sync(0xffffffffu, bx.hiy, src), __shfl_sync(0xffffffffu, bx.hiz, src)};
+            const long long sl = __shfl_sync(0xffffffffu, slot, src);
+            unsigned t = 0;
+            const float4 wr = edge_hits_warp(p, q, b, sl, lane, t);
+            if (lane == src) {
+                rec = wr;
+                ntest += t;
+            }
+        }
+        ntest += (unsigned)cnt;
+        nhit += rec.w > 0.0f ? 1u : 0u;
+        if (has) p.edge_hit[slot] = rec;
+    }
+}
+
+// Running sum of one node's response directions (Algorithm 2): adds the
+// direction from S towards the hit point P, stopping delta short.
+struct EdgeAcc {
+    float ax, ay, az;
+    int K;
+};
+__device__ __forceinline__ void edge_acc_add(EdgeAcc &a, float delta, float sx, float sy, float sz, float Px,
+                                             float Py, float Pz)
+{
+    const float wx = Px - sx, wy = Py - sy, wz = Pz - sz;
+    const float lw = sqrtf(wx * wx + wy * wy + wz * wz);
+    const float sc = lw > 0.0f ? fmaxf(lw - delta, 0.0f) / lw : 0.0f;
+    a.ax += sc * wx;
+    a.ay += sc * wy;
+    a.az += sc * wz;
+    a.K++;
+}
+
+// An edge with more hits than pass A stored: walks its candidates again, in
+// order, and adds every hit after the first (already added).  Out of line:
+// rare, and it keeps the gather's unrolled loop small.
+static __device__ __noinline__ EdgeAcc edge_rewalk(const StepParams &p, const float *xs, long long oa, long long ob,
+                                                   float sx, float sy, float sz, EdgeAcc a)
+{
+    const long long st = p.stride;
+    const float x0 = xs[oa], y0 = xs[st + oa], z0 = xs[2 * st + oa];
+    const float x1 = xs[ob], y1 = xs[st + ob], z1 = xs[2 * st + ob];
+    CollPath path;
+    if (!coll_path(p, x0, y0, z0, x1, y1, z1, path)) return a;
+    const CollBox bx = coll_box(p, x0, y0, z0, x1, y1, z1);
+    bool first = true;
+    for (int cz = bx.loz; cz <= bx.hiz; cz++)
+        for (int cy = bx.loy; cy <= bx.hiy; cy++)
+            for (int cx = bx.lox; cx <= bx.hix; cx++) {
+                const long long cell = ((long long)cz * p.gd[1] + cy) * p.gd[0] + cx;
+                const int e0 = __ldg(p.cell_start + cell), e1 = __ldg(p.cell_start + cell + 1);
+                for (int ee = e0; ee < e1; ee++) {
                     float th, f;
                     float4 A, B, C;
-                    if (coll_candidate(p, lq, e, cx, cy, cz, L.box.x, L.box.y, L.box.z, th, f, A, B, C))
-                        hv = make_float4(lq.sx + th * lq.rx, lq.sy + th * lq.ry, lq.sz + th * lq.rz, 1.0f);
-                }
-                sh.hit[wib][lane] = hv;
-                __syncwarp();
-                if (cnt > 0) {
-                    const int q0 = max(excl, r0), q1 = min(excl + cnt, r0 + 32);
-                    for (int t = q0; t < q1; t++) {
-                        const float4 P = sh.hit[wib][t - r0];
-                        if (P.w == 0.0f) continue;
-                        const float wx = P.x - sx, wy = P.y - sy, wz = P.z - sz;
-                        const float lw = sqrtf(wx * wx + wy * wy + wz * wz);
-                        const float sc = lw > 0.0f ? fmaxf(lw - p.delta, 0.0f) / lw : 0.0f;
-                        ax += sc * wx;
-                        ay += sc * wy;
-                        az += sc * wz;
-                        K++;
+                    if (!coll_candidate(p, path, ee, cx, cy, cz, bx.lox, bx.loy, bx.loz, th, f, A, B, C)) continue;
+                    if (first) {
+                        first = false;
+                        continue;
                     }
+                    const float3 hp = coll_hit_point(path, th);
+                    edge_acc_add(a, p.delta, sx, sy, sz, hp.x, hp.y, hp.z);
                 }
-                __syncwarp();
             }
+    return a;
+}
+
+// Pass B: every listed free node gathers the hits of the 12 edges whose
+// triangles contain it (in the order of edge_of_node, each edge's hits in
+// candidate order) and writes its response to p.edge_resp[i]: (position, 1),
+// or zeros without a hit.  An edge whose owner was not listed this substep
+// (stamp) cannot hit.  The stamps, then the records, of the 12 edges are
+// loaded before any is used; an edge with more than 1 + EDGE_MORE hits is
+// walked again (edge_rewalk).
+__device__ __forceinline__ void edge_gather_list(const StepParams &p, unsigned long long k, unsigned n)
+{
+    const long long st = p.stride;
+    const float *in = (k & 1ull) ? p.state1 : p.state0;
+    const float *xs = (k & 1ull) ? p.state0 : p.state1;
+    const unsigned long long stamp = k + 1ull;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int o = __ldg(p.coll_list + i);
+        const bool pinned = p.pin_bits && ((__ldg(p.pin_bits + (o >> 5)) >> (o & 31)) & 1u);
+        float4 resp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (!pinned) {
+            const int r = o / p.pitch, c = o - r * p.pitch;
+            const float sx = __ldg(in + o), sy = __ldg(in + st + o), sz = __ldg(in + 2 * st + o);
+            bool live[EDGES_PER_NODE];
+#pragma unroll
+            for (int q = 0; q < EDGES_PER_NODE; q++) {
+                const EdgeOfs e = edge_of_node(q);
+                const int ra = r + e.ar, ca = c + e.ac, rb = r + e.br, cb = c + e.bc;
+                const bool inside = ra >= 0 && ca >= 0 && rb < p.ny && cb < p.nx && ca < p.nx && cb >= 0;
+                live[q] = inside && p.edge_stamp[inside ? (long long)ra * p.pitch + ca : 0] == stamp;
+            }
+            float4 rec[EDGES_PER_NODE];
+#pragma unroll
+            for (int q = 0; q < EDGES_PER_NODE; q++) {
+                const EdgeOfs e = edge_of_node(q);
+                const long long slot = (long long)edge_kind(e.ar, e.ac, e.br, e.bc) * st +
+                                       (long long)(r + e.ar) * p.pitch + (c + e.ac);
+                rec[q] = live[q] ? p.edge_hit[slot] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            EdgeAcc acc = {0.0f, 0.0f, 0.0f, 0};
+#pragma unroll
+            for (int q = 0; q < EDGES_PER_NODE; q++) {
+                const float4 rq = rec[q];
+                if (rq.w == 0.0f) continue;
+                edge_acc_add(acc, p.delta, sx, sy, sz, rq.x, rq.y, rq.z);
+                if (rq.w == 1.0f) continue;
+                const EdgeOfs e = edge_of_node(q);
+                const long long oa = (long long)(r + e.ar) * p.pitch + (c + e.ac);
+                if (rq.w <= (float)(1 + EDGE_MORE)) {
+                    const long long slot = (long long)edge_kind(e.ar, e.ac, e.br, e.bc) * st + oa;
+                    for (int h = 1; h < (int)rq.w; h++) {
+                        const float4 P = p.edge_more[(long long)(h - 1) * 3 * st + slot];
+                        edge_acc_add(acc, p.delta, sx, sy, sz, P.x, P.y, P.z);
+                    }
+                } else {
+                    const long long ob = (long long)(r + e.br) * p.pitch + (c + e.bc);
+                    acc = edge_rewalk(p, xs, oa, ob, sx, sy, sz, acc);
+                }
+            }
+            if (acc.K > 0)
+                resp = make_float4(sx + acc.ax / (float)acc.K, sy + acc.ay / (float)acc.K, sz + acc.az / (float)acc.K,
+                                   1.0f);
         }
-        if (valid) {
-            p.edge_resp[i] = K > 0 ? make_float4(sx + ax / (float)K, sy + ay / (float)K, sz + az / (float)K, 1.0f)
-                                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        }
+        p.edge_resp[i] = resp;
     }
 }

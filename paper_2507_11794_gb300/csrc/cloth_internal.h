@@ -58,7 +58,7 @@ struct StepParams {
     float go[3];
     float ginv;
     int gd[3];
-    float mlo[3], mhi[3];      // box of the grid's non-border cells (early out)
+    float mlo[3], mhi[3];      // box of the mesh's vertices, padded by 1e-4 of its size (early out)
     int *coll_list;            // node offsets marked for the collision kernel (capacity N)
     int *coll_cloth;           // batch mode: cloth index of each entry (nullptr for one cloth)
     float *vstar;              // optional 3 planes: velocity after integration (adjoint recompute)
@@ -66,11 +66,18 @@ struct StepParams {
     uint32_t *cbits;           // with cdata: one bit per plane offset, set for the nodes that hit
     float4 *force;             // per-node force buffer of the atomic spring path, or nullptr
     float4 *edge_resp;         // edge narrow phase: per list entry (response position, hit flag), or nullptr
+    float4 *edge_hit;          // edge narrow phase: per edge (kind * stride + owner) first hit point, hit count
+    float4 *edge_more;         // edge narrow phase: CLOTH_EDGE_MORE planes of 3 x stride later hit points
+    unsigned long long *edge_stamp; // edge narrow phase: per node, 1 + the substep it was last listed in
     unsigned *coll_count;      // entries in coll_list (reset by the collision kernel)
     int coll_blocks;           // CTAs of the collision kernel
     float delta, eps, tmin, restitution;
     DevCtrl *ctrl;
 };
+
+// Edge narrow phase: hit points stored per edge after its first (an edge
+// with more hits is walked again by the gather pass).
+#define CLOTH_EDGE_MORE 3
 
 // CTAs per SM of the collision kernels (grid = SMs x this).
 #ifndef CLOTH_COLL_CTAS_PER_SM
@@ -124,6 +131,7 @@ struct DevGrid {
     int *tri_ids;      // nentries
     float4 *etri;      // 3 per entry: copy of the entry's triangle record
     int ntris;
+    float lo[3], hi[3];  // box of the triangles' vertices
 };
 
 // Host-side grid parameters (FP64 mean of the triangles' longest AABB side).
@@ -189,6 +197,9 @@ struct ClothHandle {
     float2 *wind_tab = nullptr; // ny row entries then nx column entries
     float4 *force = nullptr;    // CLOTH_FLAG_ATOMIC_SPRINGS: pitch*ny force accumulators
     float4 *edge_resp = nullptr; // CLOTH_FLAG_EDGE_COLLISION: n response slots (one per list entry)
+    float4 *edge_hit = nullptr;      // CLOTH_FLAG_EDGE_COLLISION: 3 x stride edge records
+    float4 *edge_more = nullptr;     // CLOTH_FLAG_EDGE_COLLISION: CLOTH_EDGE_MORE x 3 x stride hit points
+    unsigned long long *edge_stamp = nullptr;  // CLOTH_FLAG_EDGE_COLLISION: stride listing stamps
     DevGrid grid{};
     bool has_mesh = false;
     StepParams params{};

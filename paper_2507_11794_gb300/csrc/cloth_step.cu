@@ -247,7 +247,7 @@ __device__ __forceinline__ WalkStatics walk_statics(const StepParams &p, int sx,
 // halo: they evaluate only the springs that end in row r0 or r0 + 1.  Then
 // symplectic Euler with gravity, wind and pins (Section 3) writes rows
 // [r0, r1) of the output state and, with a surface model, the nodes whose
-// path box reaches the grid's inner cells are appended to the collision list.
+// path box reaches the box of the mesh's vertices are appended to the collision list.
 // The row loop is unrolled four times with the window's four row slots
 // renamed at each step, so the window moves without register copies.
 template <bool MESH, bool PER_SPRING>
@@ -662,14 +662,16 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kern
     }
 }
 
-// Listing of the edge narrow phase: every free node whose 3 x 3 block of
+// Listing of the edge narrow phase: every node whose 3 x 3 block of
 // nodes at the updated positions (the walk's output) has a box that reaches
-// the box of the grid's inner cells.  A node is affected only through an
-// edge of one of its triangles, all of whose vertices lie in that block, and
-// such an edge can hit a triangle of the surface model only if its box meets
-// the grid's inner cells; so every node a hit can affect is listed, however
-// far the cloth is stretched.  One thread per node; appends are aggregated
-// per warp.
+// the (padded) box of the mesh's vertices.  A node is affected only through
+// an edge of one of its triangles, all of whose vertices lie in that block,
+// and such an edge can hit a triangle of the surface model only if its box
+// meets the mesh's box; so every node a hit can affect is listed, however
+// far the cloth is stretched.  Pinned nodes are listed too: their edges are
+// tested (pass A) although they do not move.  Each listed node's stamp is set
+// to the substep, which tells pass B whose edges were tested.  One thread per
+// node; appends are aggregated per warp.
 __global__ void __launch_bounds__(256) edge_list_kernel(const __grid_constant__ StepParams p)
 {
     __shared__ unsigned long long s_k;
@@ -689,8 +691,7 @@ __global__ void __launch_bounds__(256) edge_list_kernel(const __grid_constant__ 
         if (i < n) {
             const int r = (int)(i / p.nx), c = (int)(i - (long long)r * p.nx);
             o = r * p.pitch + c;
-            const bool pinned = p.pin_bits && ((__ldg(p.pin_bits + (o >> 5)) >> (o & 31)) & 1u);
-            if (!pinned) {
+            {
                 float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
                 for (int dr = -1; dr <= 1; dr++) {
                     const int rr = r + dr;
@@ -716,17 +717,38 @@ __global__ void __launch_bounds__(256) edge_list_kernel(const __grid_constant__ 
             unsigned base = 0;
             if (lane == 0) base = atomicAdd(p.coll_count, (unsigned)__popc(m));
             base = __shfl_sync(FULL, base, 0);
-            if (want) p.coll_list[base + __popc(m & ((1u << lane) - 1u))] = o;
+            if (want) {
+                p.coll_list[base + __popc(m & ((1u << lane) - 1u))] = o;
+                p.edge_stamp[o] = k + 1ull;  // its owned edges get tested this substep
+            }
         }
     }
 }
 
-// Edge narrow phase (CLOTH_FLAG_EDGE_COLLISION): responses are computed from
-// the updated positions of all listed nodes' neighbours, so they go to a
-// scratch array first and a second kernel applies them.
-__global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_edges_kernel(const __grid_constant__ StepParams p)
+// Edge narrow phase (CLOTH_FLAG_EDGE_COLLISION): pass A tests each listed
+// node's owned edges and records their hits; pass B gathers every listed free
+// node's response from the records of its 12 edges into a scratch array; a
+// third kernel applies the responses, so no test reads a moved node.
+__global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) edge_test_kernel(const __grid_constant__ StepParams p)
 {
     __shared__ EdgeShared sh;
+    __shared__ unsigned long long s_k;
+    __shared__ unsigned s_n, s2[2];
+    pdl_launch_dependents();
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        s_k = *(volatile unsigned long long *)&p.ctrl->k;
+        s_n = *(volatile unsigned *)p.coll_count;
+        s2[0] = s2[1] = 0u;
+    }
+    __syncthreads();
+    unsigned ntest = 0, nhit = 0;
+    edge_test_list(p, sh, s_k, s_n, ntest, nhit);
+    coll_stats_add(p.ctrl, s2, s_n, ntest, nhit);
+}
+
+__global__ void __launch_bounds__(256) edge_gather_kernel(const __grid_constant__ StepParams p)
+{
     __shared__ unsigned long long s_k;
     __shared__ unsigned s_n;
     pdl_launch_dependents();
@@ -736,7 +758,7 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_edge
         s_n = *(volatile unsigned *)p.coll_count;
     }
     __syncthreads();
-    collide_edges_list(p, sh, s_k, s_n);
+    edge_gather_list(p, s_k, s_n);
 }
 
 __global__ void __launch_bounds__(256) edge_apply_kernel(const __grid_constant__ StepParams p)
@@ -988,7 +1010,9 @@ cudaError_t launch_collide(const StepParams &p, cudaStream_t s)
     if (p.edge_resp) {
         cudaError_t e = launch_k(edge_list_kernel, p.coll_blocks, 256, s, p);
         if (e != cudaSuccess) return e;
-        e = launch_k(collide_edges_kernel, p.coll_blocks, 32 * COLL_WARPS, s, p);
+        e = launch_k(edge_test_kernel, p.coll_blocks, 32 * COLL_WARPS, s, p);
+        if (e != cudaSuccess) return e;
+        e = launch_k(edge_gather_kernel, p.coll_blocks, 256, s, p);
         if (e != cudaSuccess) return e;
         return launch_k(edge_apply_kernel, p.coll_blocks, 256, s, p);
     }
