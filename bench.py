@@ -187,6 +187,94 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    libnvidia-ml, read-only queries) by a thread polling every `period_s`
+    while the timed loop runs: nvidia-smi's own loop samples about every
+    20 ms, longer than a timed loop of a few milliseconds."""
+
+    # clock-event reason bits of nvmlDeviceGetCurrentClocksEventReasons
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, uuid: str | None, period_s: float = 5e-4):
+        self.samples = []  # (perf_counter, sm MHz, reason bits)
+        self.period = period_s
+        self.dev = None
+        self.max_mhz = None
+        self.stop = threading.Event()
+        try:
+            import ctypes as C
+            self.C = C
+            self.lib = C.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                return
+            n = C.c_uint(0)
+            self.lib.nvmlDeviceGetCount_v2(C.byref(n))
+            want = (uuid or "").lower().replace("gpu-", "")
+            for i in range(n.value):
+                h = C.c_void_p()
+                if self.lib.nvmlDeviceGetHandleByIndex_v2(i, C.byref(h)) != 0:
+                    continue
+                buf = C.create_string_buffer(96)
+                self.lib.nvmlDeviceGetUUID(h, buf, 96)
+                if not want or buf.value.decode().lower().replace("gpu-", "") == want:
+                    self.dev = h
+                    break
+            if self.dev is not None:
+                m = C.c_uint(0)
+                if self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, C.byref(m)) == 0:
+                    self.max_mhz = float(m.value)
+                self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                    self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        except (OSError, AttributeError):
+            self.dev = None
+
+    def _poll(self):
+        C = self.C
+        mhz, bits = C.c_uint(0), C.c_ulonglong(0)
+        while not self.stop.is_set():
+            ok = self.lib.nvmlDeviceGetClockInfo(self.dev, 1, C.byref(mhz)) == 0
+            ok = ok and self.reasons_fn(self.dev, C.byref(bits)) == 0
+            if ok:
+                self.samples.append((time.perf_counter(), float(mhz.value), int(bits.value)))
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.dev is not None:
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self.dev is not None:
+            self.stop.set()
+            self.t.join(timeout=5)
+
+    def summary(self, window):
+        t0, t1 = window
+        inside = [s for s in self.samples if t0 <= s[0] <= t1]
+        if not inside:
+            return None
+        mhz = sorted(s[1] for s in inside)
+        reasons = sorted(nm for nm, b in self.BITS.items() if any(s[2] & b for s in inside))
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_mhz_min": mhz[0], "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(mhz), "period_ms": self.period * 1e3}
+
+
+def clock_record(smi: dict, nvml: dict | None, heat: dict) -> dict:
+    """The line's clocks: NVML's samples inside the timed loop where there
+    are any (median SM clock, union of the reasons seen), else nvidia-smi's;
+    nvidia-smi's samples of the timed loop (with the one either side) and of
+    the heat-up plus timed steps are kept beside them."""
+    out = dict(nvml) if nvml else dict(smi)
+    out["source"] = "nvml" if nvml else "nvidia-smi"
+    if nvml:
+        out["reasons"] = sorted(set(nvml["reasons"]) | set(smi.get("reasons") or []))
+    out["nvidia_smi"] = smi
+    out["heat_and_timed"] = heat
+    return out
+
+
 def dist_setup():
     import torch
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -410,12 +498,18 @@ def run_batch(args, stream):
     tuning = b.tune(10)
     b.step(2)
     b.sync()
+    stats0 = b.collision_stats()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record(stream)
     b.step(args.batch_steps)
     ev[1].record(stream)
     torch.cuda.synchronize()
     t_batch = ev[0].elapsed_time(ev[1]) / 1e3
+    stats1 = b.collision_stats()
+    nsub = args.batch_steps * sub
+    coll = {"listed_per_substep": (stats1[0] - stats0[0]) / nsub,
+            "tested_per_substep": (stats1[1] - stats0[1]) / nsub,
+            "hit_nodes_per_substep": (stats1[2] - stats0[2]) / nsub}
     for i in range(len(scenes)):
         p, _ = b.read(i)
         assert np.all(np.isfinite(p))
@@ -451,7 +545,7 @@ def run_batch(args, stream):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "scope": "walk + collision launches of one substep",
                          "algorithmic_bytes_per_substep": BYTES_PER_NODE_SUBSTEP * nodes},
-            "l2": "state (446 MB per substep) larger than L2"}
+            "collision": coll, "l2": "state (446 MB per substep) larger than L2"}
 
 
 def run_adjoint(stream):
@@ -627,7 +721,11 @@ def run_ours(args):
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(torch.cuda.current_device()) as clocks:
+    try:
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except (AttributeError, RuntimeError):
+        uuid = None
+    with ClockSampler(torch.cuda.current_device()) as clocks, NvmlSampler(uuid) as nv:
         h0 = time.perf_counter()
         for i in range(heat):
             flush.fill_(float(i))
@@ -749,7 +847,8 @@ def run_ours(args):
            "roofline": roofline, "cpu_baseline": cpu,
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 12 * N,
                    "d2h_bytes_per_step": 2 * 12 * N, "steps": ke},
-           "gpu_launches": launches, "clocks": {**clocks.summary(), "heat_and_timed": heat_clocks},
+           "gpu_launches": launches,
+           "clocks": clock_record(clocks.summary(), nv.summary((wall0, wall0 + wall)), heat_clocks),
            "collision": coll, "batch": batch, "adjoint": adjoint, "atomic_springs_ab": atomic_ab,
            "edge_narrow_phase_ab": edge_ab, "pulling_scene": pulling, "configs": legs,
            "normals": normals,

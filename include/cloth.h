@@ -290,6 +290,11 @@ int cloth_batch_set_tuning(ClothBatch *b, int32_t rows_per_warp, int32_t walk_ct
 int cloth_batch_get_tuning(ClothBatch *b, ClothBatchTuning *out);
 /* Wait for the batch's stream and report device-side error flags. */
 int cloth_batch_sync(ClothBatch *b);
+/* Running collision totals of the whole batch since create, summed over its
+ * cloths and substeps, as cloth_get_collision_stats gives them for one
+ * cloth.  Synchronises.  Any output may be NULL.  Errors:
+ * CLOTH_ERR_INVALID_ARG, CLOTH_ERR_STATE, CLOTH_ERR_CUDA. */
+int cloth_batch_get_collision_stats(ClothBatch *b, int64_t *listed, int64_t *tested, int64_t *hits);
 /* Release the batch and its cloths.  NULL-safe. */
 void cloth_batch_destroy(ClothBatch *b);
 

@@ -193,6 +193,10 @@ class ClothBatch:
     def tuning(self):
         return capi.cloth_batch_get_tuning(self.h)
 
+    def collision_stats(self):
+        """(listed, tested, hits) of the whole batch since create."""
+        return capi.cloth_batch_get_collision_stats(self.h)
+
     def sync(self):
         capi.cloth_batch_sync(self.h)
 

@@ -39,7 +39,7 @@ EXPORTS = ("cloth_create", "cloth_set_mesh", "cloth_step", "cloth_read", "cloth_
            "cloth_compute_normals",
            "cloth_batch_create", "cloth_batch_set_mesh", "cloth_batch_step", "cloth_batch_read",
            "cloth_batch_set_state", "cloth_batch_tune", "cloth_batch_set_tuning", "cloth_batch_get_tuning",
-           "cloth_batch_sync", "cloth_batch_destroy",
+           "cloth_batch_sync", "cloth_batch_get_collision_stats", "cloth_batch_destroy",
            "cloth_rollout_create", "cloth_rollout_forward", "cloth_rollout_backward", "cloth_rollout_destroy")
 
 
@@ -136,6 +136,8 @@ def lib():
         L.cloth_batch_set_tuning.argtypes = [H, C.c_int32, C.c_int32]
         L.cloth_batch_get_tuning.argtypes = [H, C.POINTER(ClothBatchTuning)]
         L.cloth_batch_sync.argtypes = [H]
+        L.cloth_batch_get_collision_stats.argtypes = [H, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                                      C.POINTER(C.c_int64)]
         L.cloth_batch_destroy.argtypes = [H]
         L.cloth_batch_destroy.restype = None
         V = C.c_void_p
@@ -325,6 +327,13 @@ def cloth_batch_get_tuning(b: int) -> ClothBatchTuning:
 
 def cloth_batch_sync(b: int):
     check(lib().cloth_batch_sync(b))
+
+
+def cloth_batch_get_collision_stats(b: int):
+    """(listed, tested, hits): running collision totals of the batch."""
+    v = [C.c_int64(0) for _ in range(3)]
+    check(lib().cloth_batch_get_collision_stats(b, *(C.byref(x) for x in v)))
+    return tuple(int(x.value) for x in v)
 
 
 def cloth_batch_destroy(b: int):

@@ -119,6 +119,13 @@ cudaError_t rebuild(ClothBatch *b)
     b->args.coll_count = &b->ctrl->coll_count;
     b->args.walk_blocks = b->sm_count * b->ctas_per_sm;
     b->args.coll_blocks = b->sm_count * CLOTH_COLL_CTAS_PER_SM;
+    // one walk variant for the whole batch when every cloth has the same one
+    int var = -1;
+    for (const StepParams &q : prm) {
+        const int v = (q.has_mesh ? BATCH_VAR_MESH : 0) | (q.ks_slot ? BATCH_VAR_PER_SPRING : 0);
+        var = var < 0 || var == v ? v : BATCH_VAR_MIXED;
+    }
+    b->args.variant = var < 0 ? BATCH_VAR_MIXED : var;
     return e;
 }
 
@@ -424,6 +431,20 @@ int cloth_batch_sync(ClothBatch *b)
     int rc = check_batch(b);
     if (rc) return rc;
     return read_batch_flags(b);
+}
+
+int cloth_batch_get_collision_stats(ClothBatch *b, int64_t *listed, int64_t *tested, int64_t *hits)
+{
+    int rc = check_batch(b);
+    if (rc) return rc;
+    unsigned long long v[3] = {0ull, 0ull, 0ull};
+    BTRY(b, cudaMemcpyAsync(v, &b->ctrl->stat_listed, sizeof(v), cudaMemcpyDeviceToHost, b->stream),
+         "read collision statistics");
+    BTRY(b, cudaStreamSynchronize(b->stream), "synchronize");
+    if (listed) *listed = (int64_t)v[0];
+    if (tested) *tested = (int64_t)v[1];
+    if (hits) *hits = (int64_t)v[2];
+    return CLOTH_OK;
 }
 
 void cloth_batch_destroy(ClothBatch *b)

@@ -107,7 +107,9 @@ struct BatchArgs {
     int *coll_list, *coll_cloth;
     unsigned *coll_count;
     int walk_blocks, coll_blocks;
+    int variant;               // BATCH_VAR_* shared by every cloth, or BATCH_VAR_MIXED
 };
+enum : int { BATCH_VAR_MESH = 1, BATCH_VAR_PER_SPRING = 2, BATCH_VAR_MIXED = 4 };
 cudaError_t launch_batch_substep(const BatchArgs &b, cudaStream_t s);
 int substep_strip_cols();
 int substep_warps_per_cta();

@@ -32,7 +32,7 @@ namespace {
 // Tuning knobs of the walk kernel (defaults chosen by measurement):
 // CTAs per SM the register budget targets, and the unroll of the row walk.
 #ifndef CLOTH_WALK_MINB
-#define CLOTH_WALK_MINB 3
+#define CLOTH_WALK_MINB 12
 #endif
 #ifndef CLOTH_WALK_UNROLL
 #define CLOTH_WALK_UNROLL 1
@@ -72,8 +72,12 @@ __device__ __forceinline__ void pdl_launch_dependents()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 #endif
 }
+// One warp per CTA: the walk's warps fill one wave, and with 4-warp CTAs
+// 403 CTAs of the 800 x 800 walk put 12 warps on two thirds of the SMs and 8
+// on the rest, so the crowded SMs set the time; single-warp CTAs spread 10
+// or 11 warps on every SM (11% faster without a mesh, 15% on the batch).
 #ifndef CLOTH_WALK_WARPS
-#define CLOTH_WALK_WARPS 4
+#define CLOTH_WALK_WARPS 1
 #endif
 constexpr int WARPS_PER_CTA = CLOTH_WALK_WARPS;
 // register budget of the walk kernels: CLOTH_WALK_MAXREG registers per thread
@@ -85,7 +89,7 @@ constexpr int WARPS_PER_CTA = CLOTH_WALK_WARPS;
 #endif
 // the batch kernel (its walk also stages each item's parameters) keeps its own
 #ifndef CLOTH_BATCH_MINB
-#define CLOTH_BATCH_MINB 2
+#define CLOTH_BATCH_MINB 12
 #endif
 constexpr int STRIP_COLS = 60;
 
@@ -808,6 +812,10 @@ __global__ void __launch_bounds__(256) edge_apply_kernel(const __grid_constant__
 // first), stages that cloth's parameters in its shared-memory slot and walks
 // the strip with the same code as the single-cloth kernel, so every cloth of a
 // batch gets exactly the arithmetic it gets when stepped alone.
+// VAR: the walk variant every cloth of the batch shares (BATCH_VAR_MESH |
+// BATCH_VAR_PER_SPRING), or BATCH_VAR_MIXED, which picks it per item; a
+// kernel with one variant inlined holds fewer registers.
+template <int VAR>
 __global__ void __launch_bounds__(32 * CLOTH_WALK_WARPS, CLOTH_BATCH_MINB) batch_substep_kernel(const BatchArgs b)
 {
     __shared__ StepParams sp[WARPS_PER_CTA];
@@ -834,7 +842,10 @@ __global__ void __launch_bounds__(32 * CLOTH_WALK_WARPS, CLOTH_BATCH_MINB) batch
         const float *in = (k & 1ull) ? p.state1 : p.state0;
         float *out = (k & 1ull) ? p.state0 : p.state1;
         const WalkStatics ws = walk_statics(p, it.y, it.z, lane);
-        if (p.has_mesh) {
+        if (VAR != BATCH_VAR_MIXED) {
+            walk_strip<(VAR & BATCH_VAR_MESH) != 0, (VAR & BATCH_VAR_PER_SPRING) != 0>(p, in, out, wbase, it.y, it.z,
+                                                                                      lane, it.x, fsum, ws);
+        } else if (p.has_mesh) {
             if (p.ks_slot) walk_strip<true, true>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum, ws);
             else walk_strip<true, false>(p, in, out, wbase, it.y, it.z, lane, it.x, fsum, ws);
         } else {
@@ -1029,7 +1040,19 @@ cudaError_t launch_substep(const StepParams &p, cudaStream_t s)
 
 cudaError_t launch_batch_substep(const BatchArgs &b, cudaStream_t s)
 {
-    cudaError_t e = launch_k(batch_substep_kernel, b.walk_blocks, 32 * WARPS_PER_CTA, s, b);
+    cudaError_t e;
+    switch (b.variant) {
+    case 0: e = launch_k(batch_substep_kernel<0>, b.walk_blocks, 32 * WARPS_PER_CTA, s, b); break;
+    case BATCH_VAR_MESH: e = launch_k(batch_substep_kernel<BATCH_VAR_MESH>, b.walk_blocks, 32 * WARPS_PER_CTA, s, b); break;
+    case BATCH_VAR_PER_SPRING:
+        e = launch_k(batch_substep_kernel<BATCH_VAR_PER_SPRING>, b.walk_blocks, 32 * WARPS_PER_CTA, s, b);
+        break;
+    case BATCH_VAR_MESH | BATCH_VAR_PER_SPRING:
+        e = launch_k(batch_substep_kernel<BATCH_VAR_MESH | BATCH_VAR_PER_SPRING>, b.walk_blocks, 32 * WARPS_PER_CTA,
+                     s, b);
+        break;
+    default: e = launch_k(batch_substep_kernel<BATCH_VAR_MIXED>, b.walk_blocks, 32 * WARPS_PER_CTA, s, b); break;
+    }
     if (e != cudaSuccess) return e;
     return launch_k(batch_collide_kernel, b.coll_blocks, 32 * COLL_WARPS, s, b);
 }
@@ -1060,7 +1083,8 @@ int substep_min_ctas()
 int batch_min_ctas()
 {
     static int cached = 0;
-    if (cached <= 0) cached = occupancy((const void *)batch_substep_kernel, CLOTH_BATCH_MINB);
+    // the most register-hungry of the variants (they share the launch bounds)
+    if (cached <= 0) cached = occupancy((const void *)batch_substep_kernel<BATCH_VAR_MIXED>, CLOTH_BATCH_MINB);
     return cached;
 }
 

@@ -78,7 +78,7 @@ def test_tuning_leaves_the_simulation_unchanged(cloth_lib):
             pb, vb = b.read(i)
             assert np.array_equal(pa, pb) and np.array_equal(va, vb)
         # every explicit tuning gives the same bits
-        for rows, ctas in ((4, 1), (32, 2), (7, 2)):
+        for rows, ctas in ((4, 1), (32, 8), (7, 3)):
             b.set_tuning(rows, ctas)
             a.step(1)
             b.step(1)
