@@ -885,9 +885,11 @@ def run_case(name: str):
         info = f"{3 * sc.substeps} launches of substep_kernel"
     elif name == "batch":
         b = P.ClothBatch(cs.config5())
+        b.set_tuning(24, b.tuning().walk_ctas_per_sm)  # the autotuner's usual pick, fixed
         b.step(2)
         b.sync()
-        info = "autotune-free batch: 2 steps x 10 substeps of batch_substep_kernel + batch_collide_kernel"
+        info = ("batch without autotuning (24 rows per warp, the default walk CTAs per SM): 2 steps x 10 "
+                "substeps of batch_substep_kernel + batch_collide_kernel")
     elif name == "grid":
         sc = cs.config3("l6")
         cl = P.Cloth(sc, mesh=False)

@@ -102,6 +102,14 @@ void free_all(ClothHandle *h)
 }  // namespace
 
 // Derives the kernel parameters from the handle's description and buffers.
+// The fractional part of x (turns) as a 64-bit binary fraction of a turn.
+static unsigned long long turn_fraction(double x)
+{
+    const double f = x - floor(x);  // [0, 1)
+    const double scaled = f * 18446744073709551616.0;  // 2^64
+    return scaled >= 18446744073709551616.0 ? 0ull : (unsigned long long)scaled;
+}
+
 void cloth_fill_params(ClothHandle *h)
 {
     const ClothDesc &d = h->desc;
@@ -141,14 +149,14 @@ void cloth_fill_params(ClothHandle *h)
     p.has_wind = d.wind.amp != 0.0f;
     p.w_amp = d.wind.amp;
     const double two_pi = 6.283185307179586;
-    p.w_omega = two_pi * (double)d.wind.freq * dt_s;
+    p.w_turn_step = turn_fraction((double)d.wind.freq * dt_s);  // omega / 2 pi, turns per substep
     double k0 = 0.0, kc = 0.0, kr = 0.0;
     for (int a = 0; a < 3; a++) {
         k0 += (double)d.wind.udir[a] * d.origin[a];
         kc += (double)d.wind.udir[a] * d.du[a];
         kr += (double)d.wind.udir[a] * d.dv[a];
     }
-    p.w_phase0 = fmod((double)d.wind.phase + (double)d.wind.kappa * k0, two_pi);
+    p.w_turn0 = turn_fraction(((double)d.wind.phase + (double)d.wind.kappa * k0) / two_pi);
     p.w_kc = (float)((double)d.wind.kappa * kc);
     p.w_kr = (float)((double)d.wind.kappa * kr);
     p.wind_rows = h->wind_tab;

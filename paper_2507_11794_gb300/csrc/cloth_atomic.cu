@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(NODE_THREADS) node_integrate_kernel(const __gr
         const unsigned long long k = *(volatile unsigned long long *)&p.ctrl->k;
         s_k = k;
         float sw = 0.0f, cw = 1.0f;
-        if (p.has_wind) sincosf((float)fmod(p.w_omega * (double)k + p.w_phase0, 6.283185307179586), &sw, &cw);
+        if (p.has_wind) sincosf(wind_base(p.w_turn_step, p.w_turn0, k), &sw, &cw);
         s_sinW = sw;
         s_cosW = cw;
     }

@@ -45,7 +45,9 @@ struct StepParams {
     // wind: phase = omega*t + phase0 + col*kc + row*kr
     int has_wind;
     float w_amp, w_dir[3];
-    double w_omega, w_phase0;
+    // omega and phase0 in turns as 64-bit binary fractions: the time phase of
+    // substep k is (w_turn_step k + w_turn0) mod 2^64, times 2 pi / 2^64
+    unsigned long long w_turn_step, w_turn0;
     float w_kc, w_kr;
     const float2 *wind_rows;   // (sin, cos) of row*kr per row
     const float2 *wind_cols;   // (sin, cos) of col*kc per column
@@ -157,6 +159,19 @@ cudaError_t launch_soa_to_aos(const float *state0, const float *state1, long lon
                               const DevCtrl *ctrl, float *aos_pos, float *aos_vel, cudaStream_t s);
 
 #ifdef __CUDACC__
+// The wind's time phase omega k + phase0 reduced to [0, 2 pi), in float.
+// omega and phase0 are held in turns as 64-bit binary fractions, so the
+// reduction modulo one turn is the wrap of integer arithmetic: no FP64 on
+// the device (a few FP64 operations cost this part more than the integer
+// multiply).  Every kernel that needs the phase calls this, so they agree bit
+// for bit.
+__device__ __forceinline__ float wind_base(unsigned long long turn_step, unsigned long long turn0,
+                                           unsigned long long k)
+{
+    const unsigned long long t = turn_step * k + turn0;         // turns, in units of 2^-64, mod 1
+    return __uint2float_rn((unsigned)(t >> 32)) * 1.46291808e-9f;  // the top 32 bits times 2 pi / 2^32
+}
+
 // Grid cell coordinate of one float coordinate: floor((x - o) * inv) in
 // float32, round-to-nearest with no contraction, clamped to [0, dim-1]
 // (NaN -> 0).  Broad-phase candidate sets are defined by this formula, so it

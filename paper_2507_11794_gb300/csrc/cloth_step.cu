@@ -585,7 +585,7 @@ __global__ void CLOTH_WALK_BOUNDS substep_kernel(const StepParams p)
         const unsigned long long k = *(volatile unsigned long long *)&p.ctrl->k;
         s_k = k;
         float wb = 0.0f;
-        if (p.has_wind) wb = (float)fmod(p.w_omega * (double)k + p.w_phase0, 6.283185307179586);
+        if (p.has_wind) wb = wind_base(p.w_turn_step, p.w_turn0, k);
         s_wbase = wb;
     }
     __syncthreads();
@@ -838,7 +838,7 @@ __global__ void __launch_bounds__(32 * CLOTH_WALK_WARPS, CLOTH_BATCH_MINB) batch
         for (int w = lane; w < (int)(sizeof(StepParams) / 4); w += 32) dst[w] = __ldg(src + w);
         __syncwarp();
         const StepParams &p = sp[wib];
-        const float wbase = p.has_wind ? (float)fmod(p.w_omega * (double)k + p.w_phase0, 6.283185307179586) : 0.0f;
+        const float wbase = p.has_wind ? wind_base(p.w_turn_step, p.w_turn0, k) : 0.0f;
         const float *in = (k & 1ull) ? p.state1 : p.state0;
         float *out = (k & 1ull) ? p.state0 : p.state1;
         const WalkStatics ws = walk_statics(p, it.y, it.z, lane);
