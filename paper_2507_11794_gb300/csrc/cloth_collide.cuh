@@ -207,9 +207,11 @@ __device__ __forceinline__ void coll_record(const StepParams &p, long long o, fl
 // (valid: whether it has one; i: its index for src.entry).  ntest (lane 0)
 // accumulates the candidate triangles the warp tested, nhit (every lane) the
 // nodes that hit.
+// With has_pre the entry's offset is pre_o, loaded by the caller (cloth 0).
 template <bool REC, class Src, class Sh>
 __device__ __forceinline__ void collide_batch(const Src &src, Sh &sh, unsigned long long k, bool valid,
-                                              unsigned long long i, float &fsum, unsigned &ntest, unsigned &nhit)
+                                              unsigned long long i, float &fsum, unsigned &ntest, unsigned &nhit,
+                                              bool has_pre = false, long long pre_o = 0)
 {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     CollLane &me = sh.lane[wib][lane];
@@ -222,7 +224,8 @@ __device__ __forceinline__ void collide_batch(const Src &src, Sh &sh, unsigned l
         float *out = nullptr;
         long long st = 0;
         if (valid) {
-            src.entry(i, cloth, o);
+            if (has_pre) o = pre_o;
+            else src.entry(i, cloth, o);
             const StepParams &p = src.params(cloth);
             st = p.stride;
             const float *in = (k & 1ull) ? p.state1 : p.state0;
@@ -360,18 +363,29 @@ __device__ __forceinline__ void collide_batch(const Src &src, Sh &sh, unsigned l
 }
 
 // The cooperative pass over a list of n entries: entry i goes to warp
-// i mod #warps (see above), 32 entries per warp and round.
+// i mod #warps (see above), 32 entries per warp and round.  has_pre: the
+// lane's entry of the first round (index coll_first_index()) is pre_o, which
+// the caller loaded before it knew n.
 template <bool REC = false, class Src, class Sh>
 __device__ __forceinline__ void collide_list(const Src &src, Sh &sh, unsigned long long k, unsigned n, float &fsum,
-                                             unsigned &ntest, unsigned &nhit)
+                                             unsigned &ntest, unsigned &nhit, bool has_pre = false,
+                                             long long pre_o = 0)
 {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned long long nw = (unsigned long long)gridDim.x * COLL_WARPS;
     const unsigned long long w = (unsigned long long)blockIdx.x * COLL_WARPS + wib;
     for (unsigned long long b0 = 0; b0 < n; b0 += 32ull * nw) {
         const unsigned long long i = b0 + (unsigned long long)lane * nw + w;
-        collide_batch<REC>(src, sh, k, i < n, i, fsum, ntest, nhit);
+        collide_batch<REC>(src, sh, k, i < n, i, fsum, ntest, nhit, has_pre && b0 == 0, pre_o);
     }
+}
+
+// The calling lane's list index in the first round of collide_list.
+__device__ __forceinline__ unsigned long long coll_first_index()
+{
+    const unsigned long long nw = (unsigned long long)gridDim.x * COLL_WARPS;
+    return (unsigned long long)(threadIdx.x & 31) * nw + (unsigned long long)blockIdx.x * COLL_WARPS +
+           (threadIdx.x >> 5);
 }
 
 // Adds a collision pass's counts to the cloth's running statistics: every

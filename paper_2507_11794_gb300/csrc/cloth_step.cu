@@ -636,6 +636,11 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kern
     __shared__ unsigned s_n, s_stat[2];
     pdl_launch_dependents();
     pdl_wait();
+    // the lane's first list entry, loaded beside the list length instead of
+    // after it (the list holds p.n entries; one past the length is stale and
+    // ignored)
+    const unsigned long long i0 = coll_first_index();
+    const long long pre_o = i0 < (unsigned long long)p.n ? (long long)__ldg(p.coll_list + i0) : 0ll;
     if (threadIdx.x == 0) {
         s_k = *(volatile unsigned long long *)&p.ctrl->k;
         s_n = *(volatile unsigned *)p.coll_count;
@@ -652,7 +657,7 @@ __global__ void __launch_bounds__(32 * COLL_WARPS, CLOTH_COLL_MINB) collide_kern
     }
     float fsum = 0.0f;
     unsigned ntest = 0u, nhit = 0u;
-    collide_list<REC>(OneClothList{p}, sh, k, s_n, fsum, ntest, nhit);
+    collide_list<REC>(OneClothList{p}, sh, k, s_n, fsum, ntest, nhit, true, pre_o);
     if (__any_sync(FULL, !isfinite(fsum)) && (threadIdx.x & 31) == 0)
         atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
     coll_stats_add(p.ctrl, s_stat, s_n, ntest, nhit);
