@@ -387,7 +387,8 @@ typedef struct ClothGridParams {
  * overlaps (on different streams, or from different threads on the same
  * device) race on the scratch and give wrong results: serialise them.  The
  * first call on each device looks the array's device address up (with that
- * device current) and should come before any stream capture on that device.
+ * device current); with lazy module loading that first call may load the
+ * library's module and allocate the array then.
  * Errors: CLOTH_ERR_INVALID_ARG (limits, capacities, a device index of 64 or
  * more), CLOTH_ERR_BAD_MESH (index out of range, non-finite vertex, 2^31 - 1
  * or more (cell, triangle) pairs), CLOTH_ERR_CUDA. */
