@@ -653,8 +653,10 @@ int cloth_rollout_create(ClothHandle *h, int32_t nsteps, int32_t checkpoint_ever
         }
         if (e == cudaSuccess) {
             cloth_fill_params(h);
-            if (h->graph) cudaGraphExecDestroy(h->graph);
-            h->graph = nullptr;
+            for (cudaGraphExec_t &g : h->graph) {
+                if (g) cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
         }
     }
     // the current state is the rollout's initial state

@@ -67,8 +67,10 @@ const int kDC[CLOTH_NDIR] = {1, 0, 1, -1, 2, 0};
 
 void free_all(ClothHandle *h)
 {
-    if (h->graph) cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
+    for (cudaGraphExec_t &g : h->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
     grid_free(&h->grid);
     cudaFree(h->state);
     cudaFree(h->pin_bits);
@@ -122,6 +124,7 @@ void cloth_fill_params(ClothHandle *h)
     p.rows_per_warp = substep_rows_per_warp(d.nx, d.ny, h->sm_count);
     substep_shape(p);
     p.stride = h->stride;
+    p.parity = -1;
     p.state0 = h->state;
     p.state1 = h->state + 6 * h->stride;
     p.pin_bits = h->pin_bits;
@@ -201,18 +204,29 @@ namespace {
 
 void invalidate_graph(ClothHandle *h)
 {
-    if (h->graph) cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
+    for (cudaGraphExec_t &g : h->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
 }
 
-// Capture one step (desc.substeps launches) as a graph on a private stream.
-cudaError_t ensure_graph(ClothHandle *h)
+// One substep launched with its buffer parity (k & 1 of that substep).
+cudaError_t launch_substep_parity(const ClothHandle *h, long long k, cudaStream_t s)
 {
-    if (h->graph) return cudaSuccess;
+    StepParams q = h->params;
+    q.parity = (int)(k & 1);
+    return launch_substep(q, s);
+}
+
+// Capture one step (desc.substeps launches) whose first substep has parity
+// par as a graph on a private stream.
+cudaError_t ensure_graph(ClothHandle *h, int par)
+{
+    if (h->graph[par]) return cudaSuccess;
     cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t le = cudaSuccess;
-    for (int s = 0; s < h->desc.substeps && le == cudaSuccess; s++) le = launch_substep(h->params, h->cap_stream);
+    for (int s = 0; s < h->desc.substeps && le == cudaSuccess; s++) le = launch_substep_parity(h, par + s, h->cap_stream);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(h->cap_stream, &g);
     if (le != cudaSuccess) {
@@ -220,7 +234,7 @@ cudaError_t ensure_graph(ClothHandle *h)
         return le;
     }
     if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(&h->graph, g, 0);
+    e = cudaGraphInstantiate(&h->graph[par], g, 0);
     cudaGraphDestroy(g);
     return e;
 }
@@ -244,6 +258,7 @@ int flags_status(unsigned flags)
 {
     if (flags & CTRL_FLAG_TIMEOUT) return fail(CLOTH_ERR_TIMEOUT, "a device-side wait timed out");
     if (flags & CTRL_FLAG_NONFINITE) return fail(CLOTH_ERR_NONFINITE, "state became non-finite");
+    if (flags & CTRL_FLAG_PARITY) return fail(CLOTH_ERR_STATE, "a substep ran on the wrong state buffer (internal)");
     return CLOTH_OK;
 }
 
@@ -492,12 +507,19 @@ int cloth_step(ClothHandle *h, int32_t nsteps)
     if (nsteps < 0) return fail(CLOTH_ERR_INVALID_ARG, "nsteps < 0");
     if (nsteps == 0) return CLOTH_OK;
     DeviceScope ds(h->device);
+    // substeps_done is the device's substep counter k as of this call's first
+    // launch (every path that queues substeps adds them), so each launch knows
+    // its buffer parity
+    const long long S = h->desc.substeps;
     if (h->desc.flags & CLOTH_FLAG_NO_GRAPH) {
-        for (int s = 0; s < nsteps; s++)
-            for (int j = 0; j < h->desc.substeps; j++) CTRY(h, launch_substep(h->params, h->stream), "substep launch");
+        for (long long j = 0; j < (long long)nsteps * S; j++)
+            CTRY(h, launch_substep_parity(h, h->substeps_done + j, h->stream), "substep launch");
     } else {
-        CTRY(h, ensure_graph(h), "graph capture");
-        for (int s = 0; s < nsteps; s++) CTRY(h, cudaGraphLaunch(h->graph, h->stream), "graph launch");
+        for (long long s = 0; s < nsteps; s++) {
+            const int par = (int)((h->substeps_done + s * S) & 1);
+            CTRY(h, ensure_graph(h, par), "graph capture");
+            CTRY(h, cudaGraphLaunch(h->graph[par], h->stream), "graph launch");
+        }
     }
     h->substeps_done += (long long)nsteps * h->desc.substeps;
     return CLOTH_OK;

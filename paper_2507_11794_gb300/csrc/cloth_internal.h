@@ -18,8 +18,10 @@ struct DevCtrl {
     unsigned long long stat_listed, stat_tested, stat_hits;
 };
 
-// NONFINITE: a stored value was NaN/Inf; TIMEOUT: a bounded wait gave up
-enum : unsigned int { CTRL_FLAG_NONFINITE = 1u, CTRL_FLAG_TIMEOUT = 2u };
+// NONFINITE: a stored value was NaN/Inf; TIMEOUT: a bounded wait gave up;
+// PARITY: a walk launched with a buffer parity that the substep counter
+// contradicts (a host bookkeeping error; its results are wrong)
+enum : unsigned int { CTRL_FLAG_NONFINITE = 1u, CTRL_FLAG_TIMEOUT = 2u, CTRL_FLAG_PARITY = 4u };
 
 // Spring directions (drow, dcol) of the canonical order; each node owns the
 // springs towards these six offsets ("forward"), and receives the other
@@ -31,6 +33,8 @@ struct StepParams {
     int nx, ny, n;
     int pitch;                 // floats per row (nx rounded up to 4): node (r,c) at r*pitch + c
     int rows_per_warp;         // rows walked by one warp
+    int parity;                // walk launches: k & 1 as the host knows it when it enqueues the launch (the
+                               // walk then picks its buffers without waiting for k), or -1: read k first
     int strips_x, strips_y;    // warp strips across columns / rows
     long long stride;          // floats between SoA planes
     float *state0, *state1;    // 6 planes each: px py pz vx vy vz
@@ -220,7 +224,7 @@ struct ClothHandle {
     DevGrid grid{};
     bool has_mesh = false;
     StepParams params{};
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one step, by the parity of its first substep
     unsigned long long params_gen = 0;  // bumped by cloth_fill_params: graphs built from older params are stale
     long long substeps_done = 0;
     bool dead = false;

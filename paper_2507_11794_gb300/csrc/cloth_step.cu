@@ -306,8 +306,6 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
     // wind: sin(base + alpha_r + beta_c) from per-row and per-column tables of
     // (sin, cos) and the addition formula; depends only on (row, col, time)
     const float2 sinB = ws.sinB, cosB = ws.cosB;
-    float sinW = 0.0f, cosW = 1.0f;
-    if (p.has_wind) sincosf(wbase, &sinW, &cosW);
     // per-row inputs, fetched one row ahead: the row's wind table entry and
     // the word holding its pin bits (shifted where it is used, so that no
     // instruction waits for the load until the next row)
@@ -322,6 +320,10 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
             }
         }
     };
+    // the time phase's sine and cosine: before the first loads in the DLR
+    // walk, after them in the others (each the faster form there)
+    float sinW = 0.0f, cosW = 1.0f;
+    if (DLR && p.has_wind) sincosf(wbase, &sinW, &cosW);
     float2 trN = ws.trN;
     unsigned pinN = ws.pinN;
 
@@ -330,6 +332,7 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
     Node2 Pa = load_row(in, st32, r, p.ny, p.pitch, cmem);
     Node2 Pb = load_row(in, st32, r + 1, p.ny, p.pitch, cmem);
     Node2 Pc = load_row(in, st32, r + 2, p.ny, p.pitch, cmem);
+    if (!DLR && p.has_wind) sincosf(wbase, &sinW, &cosW);
     Node2 Pd, Ne, Nf;
     // reactions sent into the next row by the rows above (springs (+1,0),
     // (+1,+1), (+1,-1) of row r-1 and (+2,0) of row r-2), and the (+2,0)
@@ -625,8 +628,6 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
 template <bool MESH, bool PER_SPRING, bool EDGE = false>
 __global__ void CLOTH_WALK_BOUNDS substep_kernel(const StepParams p)
 {
-    __shared__ unsigned long long s_k;
-    __shared__ float s_wbase;
     pdl_launch_dependents();
     const int lane = threadIdx.x & 31;
     const int warp = blockIdx.x * WARPS_PER_CTA + (threadIdx.x >> 5);
@@ -635,22 +636,41 @@ __global__ void CLOTH_WALK_BOUNDS substep_kernel(const StepParams p)
     WalkStatics ws{};
     if (active) ws = walk_statics(p, sx, sy, lane);  // before the wait: static tables only
     pdl_wait();
-    if (threadIdx.x == 0) {
-        const unsigned long long k = *(volatile unsigned long long *)&p.ctrl->k;
-        s_k = k;
-        float wb = 0.0f;
-        if (p.has_wind) wb = wind_base(p.w_turn_step, p.w_turn0, k);
-        s_wbase = wb;
+    // Every lane reads the substep counter itself and, with the parity known
+    // at launch (p.parity >= 0), picks its buffers without waiting for it:
+    // the row loads then overlap the counter's read, which only the wind
+    // phase and the end of the substep need.  The mesh walk (DLR) keeps the
+    // counter read by one thread and the buffers picked from it: there the
+    // other form spilled and was 1.6% slower.
+    constexpr bool DLR = MESH && !EDGE && !PER_SPRING;
+    unsigned long long k;
+    float wbase;
+    if (DLR) {
+        __shared__ unsigned long long s_k;
+        __shared__ float s_wbase;
+        if (threadIdx.x == 0) {
+            k = *(volatile unsigned long long *)&p.ctrl->k;
+            s_k = k;
+            s_wbase = p.has_wind ? wind_base(p.w_turn_step, p.w_turn0, k) : 0.0f;
+        }
+        __syncthreads();
+        k = s_k;
+        wbase = s_wbase;
+    } else {
+        k = *(volatile unsigned long long *)&p.ctrl->k;
+        wbase = p.has_wind ? wind_base(p.w_turn_step, p.w_turn0, k) : 0.0f;
     }
-    __syncthreads();
-    const unsigned long long k = s_k;
-    const float *__restrict__ in = (k & 1ull) ? p.state1 : p.state0;
-    float *__restrict__ out = (k & 1ull) ? p.state0 : p.state1;
+    const bool odd = p.parity >= 0 && !DLR ? p.parity != 0 : (k & 1ull) != 0ull;
+    const float *__restrict__ in = odd ? p.state1 : p.state0;
+    float *__restrict__ out = odd ? p.state0 : p.state1;
     float2 fsum = bc(0.0f);  // sum of every stored value: non-finite iff one of them is
-    // DLR in the mesh walk only: 2% faster there, slower without a mesh
-    if (active)
-        walk_strip<MESH && !EDGE, PER_SPRING, MESH && !EDGE && !PER_SPRING>(p, in, out, s_wbase, sx, sy, lane, 0,
-                                                                           fsum, ws);
+    // DLR (receiver-side (+1,-1) springs) in the mesh walk only: 2% faster
+    // there, slower without a mesh
+    if (active) walk_strip<MESH && !EDGE, PER_SPRING, DLR>(p, in, out, wbase, sx, sy, lane, 0, fsum, ws);
+    // the launch's parity checked against the counter after the walk (a
+    // check before it would make the walk wait for the counter)
+    if (!DLR && p.parity >= 0 && (int)(k & 1ull) != p.parity && threadIdx.x == 0)
+        atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_PARITY);
 
     const bool bad = !isfinite(fsum.x + fsum.y);
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(&p.ctrl->flags, (unsigned)CTRL_FLAG_NONFINITE);
