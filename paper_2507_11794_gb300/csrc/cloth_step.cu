@@ -547,7 +547,7 @@ __device__ __forceinline__ void walk_strip(const StepParams &p, const float *__r
                 if (!okB) {  // B is padding: keep it zero
                     xx.y = xy.y = xz.y = wx.y = wy.y = wz.y = 0.0f;
                 }
-                fsum = add2(fsum, add2(add2(add2(xx, xy), add2(xz, wx)), add2(wy, wz)));
+                fsum = add2(fsum, add2(add2(xx, xy), xz));
                 const unsigned o = (unsigned)r * (unsigned)p.pitch + (unsigned)cA;
                 if (p.vstar) {  // velocity after integration, before the response (adjoint recompute)
                     *(float2 *)(p.vstar + o) = wx;
@@ -663,7 +663,9 @@ __global__ void CLOTH_WALK_BOUNDS substep_kernel(const StepParams p)
     const bool odd = p.parity >= 0 && !DLR ? p.parity != 0 : (k & 1ull) != 0ull;
     const float *__restrict__ in = odd ? p.state1 : p.state0;
     float *__restrict__ out = odd ? p.state0 : p.state1;
-    float2 fsum = bc(0.0f);  // sum of every stored value: non-finite iff one of them is
+    // sum of the stored positions: non-finite iff one of them is or a stored
+    // velocity is (x = x0 + dt v with dt > 0; a pinned node's v is finite)
+    float2 fsum = bc(0.0f);
     // DLR (receiver-side (+1,-1) springs) in the mesh walk only: 2% faster
     // there, slower without a mesh
     if (active) walk_strip<MESH && !EDGE, PER_SPRING, DLR>(p, in, out, wbase, sx, sy, lane, 0, fsum, ws);

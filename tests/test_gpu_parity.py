@@ -292,6 +292,19 @@ def test_set_state_read_roundtrip_and_nonfinite_flag(cloth_lib):
         cl.set_state(p, v)  # clears the flag
         cl.step(1)
         cl.read()
+        # a non-finite velocity alone: the walk checks the positions it
+        # stores, and x = x0 + dt v carries it (node 500 is not pinned)
+        assert not sc.pinned[500]
+        badv = v.copy()
+        badv[500, 2] = np.inf
+        cl.set_state(p, badv)
+        cl.step(1)
+        with pytest.raises(cloth_lib.ClothError) as ei:
+            cl.read()
+        assert ei.value.code == cloth_lib.capi.CLOTH_ERR_NONFINITE
+        cl.set_state(p, v)
+        cl.step(1)
+        cl.read()
 
 
 def test_bad_mesh_is_rejected_and_previous_mesh_kept(cloth_lib):
