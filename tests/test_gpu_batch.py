@@ -48,6 +48,26 @@ def test_batch_equals_cloths_stepped_alone(cloth_lib):
         assert np.array_equal(got[i][0], ref[0]) and np.array_equal(got[i][1], ref[1]), sc.name
 
 
+def test_batch_collision_statistics_equal_the_cloths_alone(cloth_lib):
+    """Cloths starting 2-4 mm above their meshes: the batch lists, tests and
+    hits exactly what the cloths do alone (its walk decides the listing with
+    packed differences, the single walk with comparisons)."""
+    scenes = [cs.small_collision_scene(n, level=lv, gap=g, seed=s)
+              for n, lv, g, s in ((24, 2, 0.004, 5), (17, 1, 0.002, 6), (31, 2, 0.003, 7))]
+    with cloth_lib.ClothBatch(scenes) as b:
+        b.step(8)
+        got = [b.read(i)[0] for i in range(len(scenes))]
+        batch_stats = b.collision_stats()
+    single = np.zeros(3, np.int64)
+    for i, sc in enumerate(scenes):
+        with cloth_lib.Cloth(sc) as cl:
+            cl.step(8)
+            assert np.array_equal(cl.read()[0], got[i])
+            single += np.array(cl.collision_stats(), np.int64)
+    assert tuple(int(x) for x in single) == tuple(batch_stats)
+    assert batch_stats[0] > 0 and batch_stats[1] > 0 and batch_stats[2] > 0
+
+
 def test_batch_matches_oracle(cloth_lib, oracle_lib):
     scenes = _mixed_batch()
     with cloth_lib.ClothBatch(scenes) as b:
