@@ -33,3 +33,17 @@ def test_normals_of_the_initial_flat_cloth_and_minimal_grids(cloth_lib, oracle_l
             n_gpu = cl.normals().cpu().numpy()
             pos, _ = cl.read()
         np.testing.assert_allclose(n_gpu, oracle_lib.normals(pos, nx, ny), atol=1e-6)
+
+
+@pytest.mark.parametrize("nx,ny", [(30, 5), (31, 6), (60, 10), (91, 11), (2, 7), (7, 2)])
+def test_normals_at_strip_boundaries(cloth_lib, oracle_lib, nx, ny):
+    # The kernel walks strips of 30 output columns and 5 rows: sizes on and
+    # one past those boundaries, on a bumped (non-flat) cloth.
+    X0 = cs.flat_grid(nx, ny, (0.0, 0.0, 0.0), (0.05, 0.0, 0.0), (0.0, 0.05, 0.0))
+    X0 = np.asarray(X0, np.float64).reshape(-1, 3)
+    X0[:, 2] = 0.03 * np.sin(7.0 * X0[:, 0]) * np.cos(5.0 * X0[:, 1])
+    sc = make_scene(nx, ny, du=(0.05, 0, 0), dv=(0, 0.05, 0), total_mass=0.1, pos=X0.astype(np.float32))
+    with cloth_lib.Cloth(sc) as cl:
+        n_gpu = cl.normals().cpu().numpy()
+        pos, _ = cl.read()
+    np.testing.assert_allclose(n_gpu, oracle_lib.normals(pos, nx, ny), atol=2e-5)
